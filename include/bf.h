@@ -1,0 +1,235 @@
+/*
+ * bf.h — C ABI of the GB300 (sm_103a) frequency-domain coherent beamformer.
+ *
+ * The library computes, for every beam b, channel c and integration window j,
+ *
+ *     P[b][c][j] = sum_{t = j*T_int}^{(j+1)*T_int - 1} | sum_n W[c][b][n] X[n][c][t] |^2
+ *     W[c][b][n] = exp(-i 2 pi f_c (r_n . s_b) / c0),   c0 = 299 792 458 m/s
+ *
+ * from channelised complex antenna voltages X (Section 2.1 of "GPU-Powered
+ * Coherent Beamforming", Magro, Zarb Adami & Hickish: beamforming as a
+ * per-channel matrix-vector product with power detection inside the kernel;
+ * the weights are the phase terms of Eq. 1).  A partial last window
+ * (T mod T_int samples) is dropped.
+ *
+ * Conventions for every call:
+ *  - Host pointers ("h_" or documented as host) are read during the call only
+ *    and never retained.  Device pointers ("d_") are caller-owned global memory
+ *    of the current device; the library never frees them.
+ *  - The plan owns its weights, tuning choice and scratch; bf_destroy frees
+ *    them.  Nothing allocated by the library is handed to the caller.
+ *  - Calls that take a stream enqueue work on it and return without waiting
+ *    (stream-ordered, asynchronous) unless documented as synchronous.  A NULL
+ *    stream means the plan's stream given to bf_plan_create.
+ *  - Every call returns a bf_status.  On failure nothing observable has been
+ *    enqueued, and bf_last_error() returns a thread-local message.  No call
+ *    throws across the ABI.
+ *  - Device-side waits are bounded; a wait that gives up records
+ *    BF_ERR_TIMEOUT in the plan, reported by the next bf_sync.
+ *  - A plan may be used by one host thread at a time.
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bf_status {
+    BF_OK = 0,
+    BF_ERR_ARG = 1,          /* invalid argument, shape or dtype mismatch */
+    BF_ERR_NOMEM = 2,        /* device or pinned host allocation failed */
+    BF_ERR_CUDA = 3,         /* a CUDA runtime or driver call failed */
+    BF_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    BF_ERR_UNSUPPORTED = 5,  /* well-formed request this build cannot run */
+    BF_ERR_STATE = 6         /* call not valid in the plan's current state */
+} bf_status;
+
+/* Storage of one complex voltage sample (Section 2.1 uses 4-bit complex;
+ * the reduced-precision tensor-core modes are this library's).  Samples
+ * are stored as interleaved (re, im) pairs except BF_CI4. */
+typedef enum bf_dtype {
+    BF_C32 = 0,     /* 2 x float32; IEEE FP32 FFMA path, relative error <= 1e-5 */
+    BF_C16F = 1,    /* 2 x float16; FP16 tensor cores, FP32 accumulation */
+    BF_C16BF = 2,   /* 2 x bfloat16; BF16 tensor cores, FP32 accumulation */
+    BF_C8E4M3 = 3,  /* 2 x FP8 E4M3FN; FP8 tensor cores, per-beam weight scale */
+    BF_CI8 = 4,     /* 2 x int8; exact products (int8 -> FP16), per-beam weight scale */
+    BF_CI4 = 5      /* 1 byte: re in the high nibble, im in the low nibble,
+                       two's complement -8..7 (the F-engine format of Section 2.1) */
+} bf_dtype;
+
+/* Order of the voltage array. */
+typedef enum bf_layout {
+    BF_LAYOUT_CTN = 0,  /* X[c][t][n]: channel, sample, antenna fastest (the
+                           packet order of Section 3); no corner turn */
+    BF_LAYOUT_NCT = 1   /* X[n][c][t]: antenna-major; a corner-turn kernel
+                           re-lays it as [c][t][n] in plan scratch first */
+} bf_layout;
+
+/* Kernel family choice for bf_plan_set_kernel. */
+typedef enum bf_kernel {
+    BF_KERNEL_AUTO = 0, /* FP32 -> SIMT FFMA kernel; other dtypes -> tensor cores */
+    BF_KERNEL_SIMT = 1, /* CUDA-core FP32 kernel (BF_C32 only) */
+    BF_KERNEL_TC = 2    /* tcgen05/TMEM kernel (all dtypes except BF_C32) */
+} bf_kernel;
+
+typedef struct bf_plan bf_plan;
+
+/*
+ * bf_plan_create — validate the geometry and allocate a plan on the current
+ * device, then generate the weights (as bf_weights(plan, NULL)).
+ *
+ *  out       [out] receives the plan handle (NULL on failure).
+ *  n_ant     N >= 1 antennas.
+ *  pos_m     host, [N][3] doubles: antenna positions r_n in metres (any origin;
+ *            integrated powers do not depend on it).
+ *  mask      host, [N] bytes or NULL: antenna n is used iff mask[n] != 0
+ *            (sub-arraying with an antenna mask, Section 3.1).  Masked antennas
+ *            get zero weight.
+ *  n_chan    C >= 1 channels.  freqs_hz: host, [C] doubles, channel centre
+ *            frequencies f_c in Hz (> 0).
+ *  n_beam    B >= 1 beams.  dirs: host, [B][3] doubles, unit pointing vectors s_b
+ *            (|s_b| = 1 within 1e-6).
+ *  dtype     bf_dtype of the voltages (and of the tensor-core operands).
+ *  t_int     T_int >= 1 samples per integration window.
+ *  layout    bf_layout of the voltages passed to the execute calls.
+ *  stream    cudaStream_t for plan work (NULL = the legacy default stream).
+ *
+ * Errors: BF_ERR_ARG for a NULL required pointer, a non-positive size, a
+ * non-finite position or frequency, or a non-unit direction;
+ * BF_ERR_UNSUPPORTED for a dtype/shape the kernels cannot run (e.g. a
+ * tensor-core mode whose antenna count does not fill 16-byte rows);
+ * BF_ERR_NOMEM / BF_ERR_CUDA from the device.
+ */
+bf_status bf_plan_create(bf_plan **out, int n_ant, const double *pos_m,
+                         const uint8_t *mask, int n_chan, const double *freqs_hz,
+                         int n_beam, const double *dirs, int dtype, int t_int,
+                         int layout, void *stream);
+
+/*
+ * bf_weights — (re)generate the plan's weights on the device (Eq. 1; the
+ * phase argument f_c (r_n . s_b) / c0 is formed and reduced modulo one cycle
+ * in FP64, then sin/cos are taken in FP32 and the result is stored in the
+ * plan's operand format).  dirs: host [B][3] new pointing vectors (tracking
+ * beams, Section 3.1) or NULL to regenerate the current ones.  Asynchronous
+ * on the plan stream.  Errors: BF_ERR_ARG for a non-unit direction.
+ */
+bf_status bf_weights(bf_plan *plan, const double *dirs);
+
+/*
+ * bf_execute — integrated beam powers.
+ *  d_voltages  device, n_samp samples per channel in the plan's dtype and
+ *              layout: CTN -> [C][n_samp][N] samples, NCT -> [N][C][n_samp].
+ *              16-byte aligned.
+ *  n_samp      T >= 0 samples per channel.
+ *  d_power     device, float [B][C][T / T_int] (T / T_int rounded down).
+ *  stream      cudaStream_t or NULL for the plan stream.
+ * Powers are in units of |weight|^2 |voltage|^2 (unit-modulus weights, no
+ * normalisation); per-beam weight scales of the FP8/int8 modes are applied.
+ * Errors: BF_ERR_ARG (NULL pointer, n_samp < 0, misaligned pointer).
+ */
+bf_status bf_execute(bf_plan *plan, const void *d_voltages, int n_samp,
+                     float *d_power, void *stream);
+
+/*
+ * bf_execute_complex — beam voltages without detection (the S-engine style
+ * complex beam output of Section 1.1; also a test hook for the raw sums).
+ *  d_beams  device, float [B][C][n_samp][2] (re, im).
+ * Same arguments and errors as bf_execute.
+ */
+bf_status bf_execute_complex(bf_plan *plan, const void *d_voltages, int n_samp,
+                             float *d_beams, void *stream);
+
+/*
+ * bf_execute_incoherent — incoherent beam (square, then add; Section 1):
+ *  d_power  device, float [C][T / T_int], sum over the window of sum_n |X|^2
+ *           over the unmasked antennas.
+ */
+bf_status bf_execute_incoherent(bf_plan *plan, const void *d_voltages, int n_samp,
+                                float *d_power, void *stream);
+
+/*
+ * bf_execute_host — bf_execute from and to HOST memory, SYNCHRONOUS: copies
+ * the voltages to plan-owned device memory (pipelined over channel blocks on
+ * two streams so copies overlap the kernels, Section 2.2), runs the kernels
+ * and copies the powers back before returning.  Pinned host memory gives the
+ * full link rate; pageable memory works but is slower.
+ *  h_voltages  host, same layout as bf_execute's d_voltages (CTN only).
+ *  h_power     host, float [B][C][T / T_int].
+ * Errors: as bf_execute; BF_ERR_UNSUPPORTED for the NCT layout.
+ */
+bf_status bf_execute_host(bf_plan *plan, const void *h_voltages, int n_samp,
+                          float *h_power);
+
+/*
+ * bf_sync — wait for all work the plan enqueued on its streams and report any
+ * device-side timeout recorded since the last bf_sync (BF_ERR_TIMEOUT), or a
+ * CUDA error (BF_ERR_CUDA).  Clears the recorded timeout.
+ */
+bf_status bf_sync(bf_plan *plan);
+
+/* bf_destroy — free everything the plan owns (synchronises its streams first).
+ * NULL is accepted. */
+bf_status bf_destroy(bf_plan *plan);
+
+/* Thread-local message for the last failing call on this thread ("" if none).
+ * Valid until the next library call on the same thread. */
+const char *bf_last_error(void);
+
+/*
+ * bf_plan_set_kernel — choose the kernel family and the time-tile width.
+ *  kernel  bf_kernel.  tile_t: samples per tile (0 = automatic).  For the
+ *  tensor-core kernel a multiple of 16 in [16, 256] and of T_int (or of
+ *  2*T_int); for the SIMT kernel ignored.
+ * Errors: BF_ERR_UNSUPPORTED if the family cannot run the plan's dtype.
+ */
+bf_status bf_plan_set_kernel(bf_plan *plan, int kernel, int tile_t);
+
+/*
+ * bf_plan_set_input_order — the antenna order of the voltage stream differs
+ * from the array order of pos_m/mask (the F-engine lookup table of Section 3):
+ * array antenna n arrives in input slot perm[n] (host [N] ints, a permutation
+ * of 0..N-1; NULL restores the identity).  Applied to the weights, so the
+ * voltages are never gathered.  Synchronises the plan stream, then
+ * regenerates the weights.  Errors: BF_ERR_ARG if perm is not a permutation.
+ */
+bf_status bf_plan_set_input_order(bf_plan *plan, const int *perm);
+
+/*
+ * bf_plan_query — report the plan's choices (any output pointer may be NULL):
+ *  kernel (bf_kernel actually used), tile_t, beams per weight group resident
+ *  in shared memory (tensor-core kernel), and bytes of device memory owned.
+ */
+bf_status bf_plan_query(const bf_plan *plan, int *kernel, int *tile_t,
+                        int *group_tiles, size_t *device_bytes);
+
+/*
+ * bf_export_weights — copy the plan's weights, decoded from the operand
+ * format to complex float32 without the per-beam scale, into
+ *  d_w      device, float [C][B][N][2]
+ *  d_scale  device, float [C][B] per-beam scale sigma_b (1 for FP32/FP16/BF16),
+ *           or NULL.
+ * The effective weight is sigma_b * d_w.  Asynchronous on the plan stream.
+ */
+bf_status bf_export_weights(bf_plan *plan, float *d_w, float *d_scale);
+
+/*
+ * bf_corner_turn — stand-alone corner turn (Section 3 antenna reorder):
+ * antenna-major d_in[N][C][T] (complex samples of in_dtype) ->
+ * d_out[C][T][N] (out_dtype), output antenna n taken from input row perm[n]
+ * (host [N] ints, or NULL for identity).  Converting BF_C32 to a reduced
+ * dtype rounds to nearest even (FP8 saturates at +-448, int8 clips at +-127);
+ * other conversions are BF_ERR_UNSUPPORTED.  Asynchronous on `stream`.
+ */
+bf_status bf_corner_turn(const void *d_in, int in_dtype, void *d_out, int out_dtype,
+                         int n_ant, int n_chan, int n_samp, const int *perm,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H */

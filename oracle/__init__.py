@@ -240,4 +240,4 @@ def corner_turn(x_nct, perm=None):
     x = np.asarray(x_nct)
     if perm is not None:
         x = x[np.asarray(perm)]
-    return np.ascontiguousarray(np.transpose(x, (1, 2, 0)))
+    return np.ascontiguousarray(np.moveaxis(x, 0, 2))

@@ -1,0 +1,246 @@
+"""GB300 (sm_103a) frequency-domain coherent beamformer.
+
+Python binding of the C ABI declared in ``include/bf.h`` (``libbf.so``, built
+in-tree by ``paper_1412_4907_gb300.build``).  The functions keep the C names
+and only marshal arguments: every step of the computation runs in the CUDA
+kernels of the library.  Device buffers are passed as integer addresses (for
+example ``tensor.data_ptr()``) and streams as ``cudaStream_t`` integers.  If
+the library is missing, importing the binding raises: there is no fallback.
+
+``Plan`` wraps a plan with torch tensors for convenience (torch provides
+device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbf.so")
+
+BF_OK, BF_ERR_ARG, BF_ERR_NOMEM, BF_ERR_CUDA, BF_ERR_TIMEOUT, BF_ERR_UNSUPPORTED, BF_ERR_STATE = range(7)
+BF_C32, BF_C16F, BF_C16BF, BF_C8E4M3, BF_CI8, BF_CI4 = range(6)
+BF_LAYOUT_CTN, BF_LAYOUT_NCT = 0, 1
+BF_KERNEL_AUTO, BF_KERNEL_SIMT, BF_KERNEL_TC = 0, 1, 2
+
+SAMPLE_BYTES = {BF_C32: 8, BF_C16F: 4, BF_C16BF: 4, BF_C8E4M3: 2, BF_CI8: 2, BF_CI4: 1}
+STATUS_NAMES = {0: "BF_OK", 1: "BF_ERR_ARG", 2: "BF_ERR_NOMEM", 3: "BF_ERR_CUDA",
+                4: "BF_ERR_TIMEOUT", 5: "BF_ERR_UNSUPPORTED", 6: "BF_ERR_STATE"}
+
+# every entry point declared in include/bf.h, with its ctypes signature
+_P, _I, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = {
+    "bf_plan_create": [ctypes.POINTER(_P), _I, _P, _P, _I, _P, _I, _P, _I, _I, _I, _P],
+    "bf_weights": [_P, _P],
+    "bf_execute": [_P, _P, _I, _P, _P],
+    "bf_execute_complex": [_P, _P, _I, _P, _P],
+    "bf_execute_incoherent": [_P, _P, _I, _P, _P],
+    "bf_execute_host": [_P, _P, _I, _P],
+    "bf_sync": [_P],
+    "bf_destroy": [_P],
+    "bf_last_error": [],
+    "bf_plan_set_kernel": [_P, _I, _I],
+    "bf_plan_set_input_order": [_P, _P],
+    "bf_plan_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_S)],
+    "bf_export_weights": [_P, _P, _P],
+    "bf_corner_turn": [_P, _I, _P, _I, _I, _I, _I, _P, _P],
+}
+
+
+class BFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1412_4907_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, argtypes in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = argtypes
+        fn.restype = ctypes.c_char_p if name == "bf_last_error" else ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc: int):
+    if rc != BF_OK:
+        raise BFError(rc, _lib.bf_last_error().decode())
+
+
+def _host(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------- C-named thin wrappers
+def bf_plan_create(pos_m, freqs_hz, dirs, dtype: int, t_int: int, layout: int = BF_LAYOUT_CTN,
+                   mask=None, stream: int = 0) -> int:
+    pos, pp = _host(pos_m, np.float64)
+    fr, fp = _host(freqs_hz, np.float64)
+    di, dp = _host(dirs, np.float64)
+    mk, mp = _host(mask, np.uint8)
+    plan = ctypes.c_void_p()
+    _check(_lib.bf_plan_create(ctypes.byref(plan), pos.shape[0], pp, mp, fr.shape[0], fp,
+                               di.shape[0], dp, dtype, t_int, layout, stream or None))
+    return plan.value
+
+
+def bf_weights(plan: int, dirs=None):
+    di, dp = _host(dirs, np.float64)
+    _check(_lib.bf_weights(plan, dp))
+
+
+def bf_execute(plan: int, d_voltages: int, n_samp: int, d_power: int, stream: int = 0):
+    _check(_lib.bf_execute(plan, d_voltages, n_samp, d_power, stream or None))
+
+
+def bf_execute_complex(plan: int, d_voltages: int, n_samp: int, d_beams: int, stream: int = 0):
+    _check(_lib.bf_execute_complex(plan, d_voltages, n_samp, d_beams, stream or None))
+
+
+def bf_execute_incoherent(plan: int, d_voltages: int, n_samp: int, d_power: int, stream: int = 0):
+    _check(_lib.bf_execute_incoherent(plan, d_voltages, n_samp, d_power, stream or None))
+
+
+def bf_execute_host(plan: int, h_voltages: int, n_samp: int, h_power: int):
+    _check(_lib.bf_execute_host(plan, h_voltages, n_samp, h_power))
+
+
+def bf_sync(plan: int):
+    _check(_lib.bf_sync(plan))
+
+
+def bf_destroy(plan: int):
+    _check(_lib.bf_destroy(plan))
+
+
+def bf_last_error() -> str:
+    return _lib.bf_last_error().decode()
+
+
+def bf_plan_set_kernel(plan: int, kernel: int, tile_t: int = 0):
+    _check(_lib.bf_plan_set_kernel(plan, kernel, tile_t))
+
+
+def bf_plan_set_input_order(plan: int, perm=None):
+    pa, pp = _host(perm, np.int32)
+    _check(_lib.bf_plan_set_input_order(plan, pp))
+
+
+def bf_plan_query(plan: int) -> dict:
+    k, t, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nb = ctypes.c_size_t()
+    _check(_lib.bf_plan_query(plan, ctypes.byref(k), ctypes.byref(t), ctypes.byref(g), ctypes.byref(nb)))
+    return {"kernel": k.value, "tile_t": t.value, "group_tiles": g.value, "device_bytes": nb.value}
+
+
+def bf_export_weights(plan: int, d_w: int, d_scale: int = 0):
+    _check(_lib.bf_export_weights(plan, d_w, d_scale or None))
+
+
+def bf_corner_turn(d_in: int, in_dtype: int, d_out: int, out_dtype: int, n_ant: int, n_chan: int,
+                   n_samp: int, perm=None, stream: int = 0):
+    pa, pp = _host(perm, np.int32)
+    _check(_lib.bf_corner_turn(d_in, in_dtype, d_out, out_dtype, n_ant, n_chan, n_samp, pp,
+                               stream or None))
+
+
+# ------------------------------------------------------------ torch helper
+class Plan:
+    """A beamforming plan on the current CUDA device.  Voltages are torch
+    tensors whose bytes hold the plan's dtype (for example float16 [C][T][2N]
+    for BF_C16F, int8 [C][T][2N] for BF_CI8, uint8 [C][T][N] for BF_CI4)."""
+
+    def __init__(self, pos_m, freqs_hz, dirs, dtype: int, t_int: int, layout: int = BF_LAYOUT_CTN,
+                 mask=None, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.N = int(np.asarray(pos_m).shape[0])
+        self.C = int(np.asarray(freqs_hz).shape[0])
+        self.B = int(np.asarray(dirs).shape[0])
+        self.dtype, self.t_int, self.layout = dtype, t_int, layout
+        self.handle = bf_plan_create(pos_m, freqs_hz, dirs, dtype, t_int, layout, mask,
+                                     self.stream.cuda_stream)
+
+    def close(self):
+        if self.handle:
+            bf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_samp(self, x) -> int:
+        per = SAMPLE_BYTES[self.dtype] * self.N * self.C
+        nbytes = x.numel() * x.element_size()
+        if nbytes % per:
+            raise ValueError("voltage tensor size does not match the plan")
+        return nbytes // per
+
+    def execute(self, x, out=None, n_samp=None):
+        T = self.n_samp(x) if n_samp is None else n_samp
+        if out is None:
+            out = self._torch.empty((self.B, self.C, T // self.t_int), dtype=self._torch.float32,
+                                    device=x.device)
+        bf_execute(self.handle, x.data_ptr(), T, out.data_ptr(), self.stream.cuda_stream)
+        return out
+
+    def execute_complex(self, x, out=None, n_samp=None):
+        T = self.n_samp(x) if n_samp is None else n_samp
+        if out is None:
+            out = self._torch.empty((self.B, self.C, T, 2), dtype=self._torch.float32, device=x.device)
+        bf_execute_complex(self.handle, x.data_ptr(), T, out.data_ptr(), self.stream.cuda_stream)
+        return out
+
+    def execute_incoherent(self, x, out=None, n_samp=None):
+        T = self.n_samp(x) if n_samp is None else n_samp
+        if out is None:
+            out = self._torch.empty((self.C, T // self.t_int), dtype=self._torch.float32, device=x.device)
+        bf_execute_incoherent(self.handle, x.data_ptr(), T, out.data_ptr(), self.stream.cuda_stream)
+        return out
+
+    def execute_host(self, x_host, out_host=None, n_samp=None):
+        """x_host: numpy array or pinned CPU tensor; returns the host powers."""
+        torch = self._torch
+        if isinstance(x_host, np.ndarray):
+            x_host = torch.from_numpy(np.ascontiguousarray(x_host))
+        T = self.n_samp(x_host) if n_samp is None else n_samp
+        if out_host is None:
+            out_host = torch.empty((self.B, self.C, T // self.t_int), dtype=torch.float32)
+        bf_execute_host(self.handle, x_host.data_ptr(), T, out_host.data_ptr())
+        return out_host
+
+    def weights(self, dirs=None):
+        bf_weights(self.handle, dirs)
+
+    def set_kernel(self, kernel: int, tile_t: int = 0):
+        bf_plan_set_kernel(self.handle, kernel, tile_t)
+
+    def set_input_order(self, perm):
+        bf_plan_set_input_order(self.handle, perm)
+
+    def query(self) -> dict:
+        return bf_plan_query(self.handle)
+
+    def export_weights(self):
+        torch = self._torch
+        w = torch.empty((self.C, self.B, self.N, 2), dtype=torch.float32, device="cuda")
+        s = torch.empty((self.C, self.B), dtype=torch.float32, device="cuda")
+        bf_export_weights(self.handle, w.data_ptr(), s.data_ptr())
+        return w, s
+
+    def sync(self):
+        bf_sync(self.handle)

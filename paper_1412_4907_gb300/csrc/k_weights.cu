@@ -1,0 +1,305 @@
+// Weight generation (Eq. 1): W[c][b][n] = exp(-i 2 pi f_c (r_n . s_b) / c0).
+//
+// The phase in cycles, f_c * tau[b][n] with tau = (r_n . s_b) / c0, is formed
+// and reduced to [-1/2, 1/2] in FP64: a 200 m baseline at 416 MHz spans ~277
+// cycles, and FP32 would keep only ~1.7e-5 cycle of the fraction.  The
+// reduced phase is exact in FP32 to 2^-25 cycle, so sin/cos are taken in
+// FP32 (sincospif).  The weights are computed once per plan or pointing
+// update and reused for every sample of every chunk (Section 2.1).
+//
+// Tensor-core storage: each beam owns two operand rows of K = 2N real
+// elements against voltages stored as interleaved (Re X, Im X) pairs:
+//   re row: (Re W, -Im W) per antenna  -> row . x = Re(W X)
+//   im row: (Im W,  Re W) per antenna  -> row . x = Im(W X)
+// Within a 128-row tile (64 beams) rows are grouped by 32: beams 16g..16g+15
+// take rows 32g..32g+15 (re) and 32g+16..32g+31 (im), so the two rows of a
+// beam land in the same warp of the epilogue, 16 lanes apart.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+__global__ void k_delays(const double *__restrict__ pos, const double *__restrict__ dirs, int N, int B,
+                         double *__restrict__ tau)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * B) return;
+    int b = i / N, n = i % N;
+    double rs = pos[3 * n] * dirs[3 * b] + pos[3 * n + 1] * dirs[3 * b + 1] + pos[3 * n + 2] * dirs[3 * b + 2];
+    tau[i] = rs / kC0;
+}
+
+__device__ __forceinline__ float2 weight_at(double f, const double *__restrict__ tau, const uint8_t *mask,
+                                            int b, int n, int N, int B)
+{
+    if (b >= B || n >= N || (mask && !mask[n])) return make_float2(0.f, 0.f);
+    double ph = f * tau[(size_t)b * N + n];     // cycles
+    double r = ph - rint(ph);                   // [-1/2, 1/2]
+    float s, c;
+    sincospif(static_cast<float>(2.0 * r), &s, &c);
+    return make_float2(c, -s);                  // exp(-i 2 pi ph)
+}
+
+// The same weight with sin/cos in FP64 (used only near rounding boundaries).
+__device__ __forceinline__ double2 weight_at64(double f, const double *__restrict__ tau, const uint8_t *mask,
+                                               int b, int n, int N, int B)
+{
+    if (b >= B || n >= N || (mask && !mask[n])) return make_double2(0.0, 0.0);
+    double ph = f * tau[(size_t)b * N + n];
+    double r = ph - rint(ph);
+    double s, c;
+    sincospi(2.0 * r, &s, &c);
+    return make_double2(c, -s);
+}
+
+// Storage formats of the tensor-core weight rows.  Every format rounds to
+// nearest, ties to even; FP8 saturates; the int8 reading keeps integers
+// |q| <= 127 (exact in FP16).
+enum { kFmtSimt = 0, kFmtF16 = 1, kFmtBF16 = 2, kFmtE4M3 = 3, kFmtI8 = 4 };
+
+template <int FMT>
+struct Quant;
+template <>
+struct Quant<kFmtF16> {
+    using T = uint16_t;
+    static constexpr float qmax = 0.f;
+    static constexpr T mag = 0x7FFF;
+    __device__ static T q(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    __device__ static T q(double x) { return __half_as_ushort(__double2half(x)); }
+};
+template <>
+struct Quant<kFmtBF16> {
+    using T = uint16_t;
+    static constexpr float qmax = 0.f;
+    static constexpr T mag = 0x7FFF;
+    __device__ static T q(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    __device__ static T q(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
+};
+template <>
+struct Quant<kFmtE4M3> {
+    using T = uint8_t;
+    static constexpr float qmax = 448.f;
+    static constexpr T mag = 0x7F;
+    __device__ static T q(float x) { return (T)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
+    __device__ static T q(double x) { return (T)__nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
+};
+template <>
+struct Quant<kFmtI8> {
+    using T = uint16_t;   // stored as FP16 integers
+    static constexpr float qmax = 127.f;
+    static constexpr T mag = 0x7FFF;
+    __device__ static T q(float x) { return __half_as_ushort(__float2half_rn(fminf(fmaxf(rintf(x), -127.f), 127.f))); }
+    __device__ static T q(double x) { return __half_as_ushort(__double2half(fmin(fmax(rint(x), -127.0), 127.0))); }
+};
+
+// Two stored codes of the same value (+0 and -0 count as equal).
+template <class Q>
+__device__ __forceinline__ bool same_value(typename Q::T a, typename Q::T b)
+{
+    return a == b || ((a & Q::mag) == 0 && (b & Q::mag) == 0);
+}
+
+// One warp per (channel, beam slot).
+template <int FMT>
+__global__ void k_weights_simt(const double *__restrict__ freqs, const double *__restrict__ tau,
+                               const uint8_t *__restrict__ mask, int N, int B, int b_pad, float2 *__restrict__ w,
+                               float *__restrict__ wscale, float *__restrict__ wsig)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int c = blockIdx.y;
+    if (b >= b_pad) return;
+    const double f = freqs[c];
+    if (lane == 0) {
+        wscale[(size_t)c * b_pad + b] = 1.f;
+        wsig[(size_t)c * b_pad + b] = 1.f;
+    }
+    float2 *row = w + ((size_t)c * b_pad + b) * N;
+    for (int n = lane; n < N; n += 32) row[n] = weight_at(f, tau, mask, b, n, N, B);
+}
+
+// Tensor-core rows.  Each stored component is first rounded from the FP32
+// weight; when that value lies within the FP32 error (4e-7, in weight units)
+// of a rounding boundary of the format, the component (unscaled formats) or
+// the whole beam (scaled formats, whose scale depends on every antenna) is
+// recomputed in FP64 and rounded once from double, so the stored value is
+// the format's rounding of the exact weight.
+template <int FMT>
+__global__ void k_weights_tc(const double *__restrict__ freqs, const double *__restrict__ tau,
+                             const uint8_t *__restrict__ mask, int N, int B, int b_pad, int k_pad,
+                             void *__restrict__ w, float *__restrict__ wscale, float *__restrict__ wsig)
+{
+    using Q = Quant<FMT>;
+    using T = typename Q::T;
+    constexpr bool scaled = Q::qmax > 0.f;
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int c = blockIdx.y;
+    if (b >= b_pad) return;
+    const double f = freqs[c];
+    const int n_cols = k_pad / 2;
+
+    float sig = 1.f;
+    if (scaled) {
+        float mx = 0.f;
+        for (int n = lane; n < N; n += 32) {
+            float2 v = weight_at(f, tau, mask, b, n, N, B);
+            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (mx > 0.f) sig = mx / Q::qmax;
+    }
+    const float delta = 4e-7f / sig;   // FP32 weight error bound in stored units
+
+    const int mt = b / kBeamsPerMTile, bi = b % kBeamsPerMTile;
+    const int row_re = mt * kRowsPerMTile + (bi >> 4) * 32 + (bi & 15);
+    const size_t m_pad = (size_t)(b_pad / kBeamsPerMTile) * kRowsPerMTile;
+    T *p_re = reinterpret_cast<T *>(w) + ((size_t)c * m_pad + row_re) * k_pad;
+    T *p_im = p_re + (size_t)16 * k_pad;   // the im row sits 16 rows below
+    auto put = [&](int n, T qre, T qim, T qim_neg) {
+        p_re[2 * n] = qre;       // re row: ( Re W, -Im W)
+        p_re[2 * n + 1] = qim_neg;
+        p_im[2 * n] = qim;       // im row: ( Im W,  Re W)
+        p_im[2 * n + 1] = qre;
+    };
+    bool redo = false;
+    for (int n = lane; n < n_cols; n += 32) {
+        float2 v = weight_at(f, tau, mask, b, n, N, B);
+        if (v.x == 0.f && v.y == 0.f) {   // masked antenna, padding beam or padding column
+            put(n, T(0), T(0), T(0));
+            continue;
+        }
+        float re = v.x / sig, im = v.y / sig;
+        const float dre = delta + 4e-7f * fabsf(re), dim = delta + 4e-7f * fabsf(im);
+        const bool near = !same_value<Q>(Q::q(re - dre), Q::q(re + dre)) ||
+                          !same_value<Q>(Q::q(im - dim), Q::q(im + dim));
+        if (near && !scaled) {
+            double2 d = weight_at64(f, tau, mask, b, n, N, B);
+            put(n, Q::q(d.x), Q::q(d.y), Q::q(-d.y));
+        } else {
+            put(n, Q::q(re), Q::q(im), Q::q(-im));
+        }
+        redo |= near;
+    }
+    if (scaled && __any_sync(0xffffffffu, redo)) {
+        double mx = 0.0;
+        for (int n = lane; n < N; n += 32) {
+            double2 d = weight_at64(f, tau, mask, b, n, N, B);
+            mx = fmax(mx, fmax(fabs(d.x), fabs(d.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const double sig64 = mx > 0.0 ? mx / (double)Q::qmax : 1.0;
+        for (int n = lane; n < n_cols; n += 32) {
+            double2 d = weight_at64(f, tau, mask, b, n, N, B);
+            const double re = d.x / sig64, im = d.y / sig64;
+            put(n, Q::q(re), Q::q(im), Q::q(-im));
+        }
+        sig = (float)sig64;
+    }
+    if (lane == 0) {
+        wscale[(size_t)c * b_pad + b] = sig * sig;
+        wsig[(size_t)c * b_pad + b] = sig;
+    }
+}
+
+// Decode the stored weights back to complex float32 [C][B][N] (without scale).
+template <int FMT>
+__global__ void k_export(const void *__restrict__ w, const float *__restrict__ wsig, int C, int N, int B,
+                         int b_pad, int k_pad, float *__restrict__ out, float *__restrict__ scale)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)C * B * N;
+    if (i >= total) return;
+    int n = (int)(i % N);
+    int b = (int)((i / N) % B);
+    int c = (int)(i / ((size_t)N * B));
+    float2 v;
+    if (FMT == 0) {
+        v = reinterpret_cast<const float2 *>(w)[((size_t)c * b_pad + b) * N + n];
+    } else {
+        const int mt = b / kBeamsPerMTile, bi = b % kBeamsPerMTile;
+        const int row_re = mt * kRowsPerMTile + (bi >> 4) * 32 + (bi & 15);
+        const size_t m_pad = (size_t)(b_pad / kBeamsPerMTile) * kRowsPerMTile;
+        const size_t e = ((size_t)c * m_pad + row_re) * k_pad + 2 * n;
+        float a0, a1;
+        if (FMT == kFmtF16 || FMT == kFmtI8) {
+            __half2 h = reinterpret_cast<const __half2 *>(w)[e / 2];
+            a0 = __low2float(h);
+            a1 = __high2float(h);
+        } else if (FMT == kFmtBF16) {
+            __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162 *>(w)[e / 2];
+            a0 = __low2float(h);
+            a1 = __high2float(h);
+        } else {
+            const __nv_fp8_storage_t *p = reinterpret_cast<const __nv_fp8_storage_t *>(w);
+            a0 = __half2float(__half(__nv_cvt_fp8_to_halfraw(p[e], __NV_E4M3)));
+            a1 = __half2float(__half(__nv_cvt_fp8_to_halfraw(p[e + 1], __NV_E4M3)));
+        }
+        v = make_float2(a0, -a1);
+    }
+    out[2 * i] = v.x;
+    out[2 * i + 1] = v.y;
+    if (scale && n == 0) scale[(size_t)c * B + b] = wsig[(size_t)c * b_pad + b];
+}
+
+static int fmt_code(const bf_plan *p)
+{
+    if (p->wf.simt) return kFmtSimt;
+    if (p->wf.op == kOpBF16) return kFmtBF16;
+    if (p->wf.op == kOpE4M3) return kFmtE4M3;
+    if (p->wf.qmax == 127.f) return kFmtI8;
+    return kFmtF16;
+}
+
+cudaError_t launch_delays(bf_plan *p, cudaStream_t s)
+{
+    int total = p->N * p->B;
+    k_delays<<<(total + 255) / 256, 256, 0, s>>>(p->d_pos, p->d_dirs, p->N, p->B, p->d_tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(bf_plan *p, cudaStream_t s)
+{
+    dim3 grid((p->wf.b_pad + 7) / 8, p->C);
+    const WeightFormat &f = p->wf;
+#define BF_W_LAUNCH(F)                                                                                 \
+    k_weights_tc<F><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_mask, p->N, p->B, f.b_pad, f.k_pad, \
+                                         p->d_w, p->d_wscale, p->d_wsig)
+    switch (fmt_code(p)) {
+    case kFmtSimt:
+        k_weights_simt<0><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_mask, p->N, p->B, f.b_pad,
+                                               (float2 *)p->d_w, p->d_wscale, p->d_wsig);
+        break;
+    case kFmtF16: BF_W_LAUNCH(kFmtF16); break;
+    case kFmtBF16: BF_W_LAUNCH(kFmtBF16); break;
+    case kFmtE4M3: BF_W_LAUNCH(kFmtE4M3); break;
+    default: BF_W_LAUNCH(kFmtI8); break;
+    }
+#undef BF_W_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_weights(bf_plan *p, float *d_w, float *d_scale, cudaStream_t s)
+{
+    size_t total = (size_t)p->C * p->B * p->N;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    const WeightFormat &f = p->wf;
+#define BF_E_LAUNCH(F)                                                                                       \
+    k_export<F><<<blocks, 256, 0, s>>>(p->d_w, p->d_wsig, p->C, p->N, p->B, f.b_pad, f.k_pad, d_w, d_scale)
+    switch (fmt_code(p)) {
+    case kFmtSimt: BF_E_LAUNCH(kFmtSimt); break;
+    case kFmtF16: BF_E_LAUNCH(kFmtF16); break;
+    case kFmtBF16: BF_E_LAUNCH(kFmtBF16); break;
+    case kFmtE4M3: BF_E_LAUNCH(kFmtE4M3); break;
+    default: BF_E_LAUNCH(kFmtI8); break;
+    }
+#undef BF_E_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace bfi

@@ -1,0 +1,407 @@
+"""GPU parity of every kernel against the FP64 oracle, through the C ABI.
+
+Expected values come only from ``oracle`` on the same seeded inputs.
+Tolerances (with the floor of ``helpers.rel_errors``):
+  FP32 (SIMT, IEEE FFMA)                        max 1e-5, L2 1e-5 (the stated bar)
+  FP16 / BF16 / int8 / int4 on tensor cores     max 1e-4, L2 1e-5
+  FP8 E4M3 on tensor cores                      max 1e-3, L2 1e-4
+against an oracle whose weights are the format's rounding of the exact
+weights and whose voltages are the stored values (the kernel error).  The
+products of the 16-bit and integer modes are exact in FP32 and the integer
+sums are exact below 2^24, so the residual is FP32 accumulation and window
+summation (~K 2^-24 relative per sum); FP8 products are exact too but the
+tensor-core accumulation of kind::f8f6f4 is allowed a wider margin.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import oracle_power_for_mode, rel_errors, small_scene, stored_voltages
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {synth.C32: (1e-5, 1e-5), synth.C16F: (1e-4, 1e-5), synth.C16BF: (1e-4, 1e-5),
+       synth.CI8: (1e-4, 1e-5), synth.CI4: (1e-4, 1e-5), synth.C8E4M3: (1e-3, 1e-4)}
+MODES_TC = [synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8, synth.CI4]
+ERRLOG = []
+
+
+@pytest.fixture(scope="module")
+def bf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1412_4907_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dump_errors():
+    yield
+    path = os.environ.get("BF_PARITY_LOG")
+    if path and ERRLOG:
+        with open(path, "w") as f:
+            json.dump(ERRLOG, f, indent=1)
+
+
+def record(name, mx, l2, **kw):
+    ERRLOG.append({"case": name, "max_rel": mx, "l2_rel": l2, **kw})
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_power(bf, scene, dirs, t_int, mode, x, layout=0, mask=None, T=None, tile=0):
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, mode, t_int, layout, mask=mask)
+    if tile:
+        plan.set_kernel(bf.BF_KERNEL_TC, tile)
+    out = plan.execute(dev(x), n_samp=T)
+    plan.sync()
+    res = out.cpu().numpy()
+    q = plan.query()
+    plan.close()
+    return res, q
+
+
+def check(name, P, P_ref, mode, **kw):
+    mx, l2 = rel_errors(P, P_ref)
+    record(name, mx, l2, mode=synth.MODE_NAMES[mode], **kw)
+    tmx, tl2 = TOL[mode]
+    assert P.shape == P_ref.shape
+    assert np.all(np.isfinite(P))
+    assert mx <= tmx and l2 <= tl2, (name, mx, l2)
+
+
+# ------------------------------------------------------------------ weights
+def test_weights_fp32_match_fp64(bf):
+    scene, dirs, _ = synth.config1()
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C32, 16)
+    w, s = plan.export_weights()
+    plan.sync()
+    W = w.cpu().numpy().astype(np.float64)
+    W = W[..., 0] + 1j * W[..., 1]
+    ref = oracle.weights(scene.pos, scene.freqs, dirs)
+    err = np.max(np.abs(W - ref))
+    record("weights_fp32", float(err), 0.0, mode="c32")
+    assert err < 5e-7
+    assert np.all(s.cpu().numpy() == 1.0)
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", [synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8])
+def test_weights_quantised_are_the_rounding_of_the_exact_weights(bf, mode):
+    scene = small_scene(n_ant=64, n_chan=8, grid=False, extent=200.0)
+    dirs = synth.beam_grid(16, 12)
+    mask = np.ones(64, np.uint8)
+    mask[[5, 40]] = 0
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, mode, 64, mask=mask)
+    w, s = plan.export_weights()
+    plan.sync()
+    got = w.cpu().numpy().astype(np.float64)
+    got = got[..., 0] + 1j * got[..., 1]
+    sig = s.cpu().numpy().astype(np.float64)
+    W = oracle.weights(scene.pos, scene.freqs, dirs, mask)
+    _, sig_ref, stored = oracle.quantised_weights(W, mode)
+    mism = int(np.sum(got != stored))
+    record("weights_stored", float(mism), 0.0, mode=synth.MODE_NAMES[mode])
+    assert mism == 0
+    assert np.allclose(sig, sig_ref, rtol=5e-7, atol=0)
+    plan.close()
+
+
+# ---------------------------------------------------------------- FP32 path
+def test_config1_fp32_full(bf):
+    """The small FP32 configuration in full: 32 antennas, 64 channels,
+    128 beams, 1024 samples, T_int = 16, against the FP64 oracle."""
+    scene, dirs, t_int = synth.config1()
+    x, X64 = stored_voltages(scene, synth.C32)
+    P, q = run_power(bf, scene, dirs, t_int, synth.C32, x)
+    assert q["kernel"] == bf.BF_KERNEL_SIMT
+    P_ref = oracle.power(oracle.weights(scene.pos, scene.freqs, dirs), X64, t_int)
+    check("config1_fp32", P, P_ref, synth.C32)
+    assert int(np.argmax(P.sum(axis=(1, 2)))) == 37
+
+
+@pytest.mark.parametrize("t_int", [1, 7, 16, 100])
+def test_fp32_windows_and_ragged_shapes(bf, t_int):
+    scene = small_scene(n_ant=13, n_chan=2, n_samp=333, grid=False)
+    dirs = synth.beam_grid(9, 9)[:70]
+    x, X64 = stored_voltages(scene, synth.C32)
+    P, _ = run_power(bf, scene, dirs, t_int, synth.C32, x)
+    check(f"fp32_tint{t_int}", P, oracle_power_for_mode(scene, dirs, t_int, synth.C32, X64), synth.C32)
+
+
+def test_fp32_complex_and_nct(bf):
+    scene = small_scene(n_ant=20, n_chan=3, n_samp=200, grid=False)
+    dirs = synth.beam_grid(10, 7)
+    x, X64 = stored_voltages(scene, synth.C32)
+    W = oracle.weights(scene.pos, scene.freqs, dirs)
+    Bref = oracle.beams(W, X64)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C32, 8)
+    Bg = plan.execute_complex(dev(x)).cpu().numpy()
+    Bg = Bg[..., 0] + 1j * Bg[..., 1]
+    err = np.max(np.abs(Bg - Bref)) / np.max(np.abs(Bref))
+    record("fp32_complex", float(err), 0.0, mode="c32")
+    assert err < 2e-6
+    plan.close()
+    xn = synth.to_nct(x, synth.C32)
+    Pn, _ = run_power(bf, scene, dirs, 8, synth.C32, xn, layout=bf.BF_LAYOUT_NCT)
+    check("fp32_nct", Pn, oracle.power(W, X64, 8), synth.C32)
+
+
+# ---------------------------------------------------------- tensor-core path
+@pytest.mark.parametrize("mode", MODES_TC)
+def test_tc_modes_ragged(bf, mode):
+    """BEST-2 array, 200 beams (4 M tiles, last one partial), 1000 samples
+    (4 time tiles, ragged; the 40-sample tail is dropped), 3 channels."""
+    sigma = 16.0 if mode in (synth.CI8, synth.C8E4M3) else (2.0 if mode == synth.CI4 else 0.7071)
+    scene = small_scene(n_ant=32, n_chan=3, n_samp=1000, sigma=sigma)
+    dirs = synth.beam_grid(20, 10)
+    x, X64 = stored_voltages(scene, mode)
+    P, q = run_power(bf, scene, dirs, 64, mode, x)
+    assert q["kernel"] == bf.BF_KERNEL_TC
+    P_ref = oracle_power_for_mode(scene, dirs, 64, mode, X64)
+    check("tc_ragged", P, P_ref, mode)
+    # end-to-end error against the unquantised FP64 beamformer (reported)
+    x32 = synth.voltages(scene, synth.C32).view(np.complex64).astype(np.complex128)
+    P64 = oracle.power(oracle.weights(scene.pos, scene.freqs, dirs), x32, 64)
+    mx, l2 = rel_errors(P, P64)
+    record("tc_ragged_vs_fp64", mx, l2, mode=synth.MODE_NAMES[mode])
+
+
+@pytest.mark.parametrize("n_ant,n_beam,n_samp,t_int,mode", [
+    (4, 1, 64, 64, synth.C16F),          # smallest tensor-core shape
+    (8, 65, 300, 16, synth.C16F),        # T_int 16, two M tiles, ragged
+    (16, 64, 512, 48, synth.C16BF),      # lcm(16, 48) tiles
+    (64, 130, 700, 64, synth.C16F),      # two K blocks
+    (128, 70, 400, 64, synth.C16F),      # four K blocks, narrower time tile
+    (32, 33, 250, 10, synth.C16F),       # generic window path (T_int % 16 != 0)
+    (32, 100, 256, 256, synth.C16F),     # one window per tile, no column split
+    (16, 40, 640, 32, synth.C8E4M3),     # FP8 with a padded K block
+    (40, 50, 333, 16, synth.CI8),
+    (32, 64, 100, 128, synth.C16F),      # T < tile
+])
+def test_tc_shapes(bf, n_ant, n_beam, n_samp, t_int, mode):
+    sigma = 16.0 if mode in (synth.CI8, synth.C8E4M3) else 0.7071
+    scene = small_scene(n_ant=n_ant, n_chan=2, n_samp=n_samp, grid=False, sigma=sigma)
+    dirs = synth.beam_grid(11, 12)[:n_beam]
+    x, X64 = stored_voltages(scene, mode)
+    P, q = run_power(bf, scene, dirs, t_int, mode, x)
+    check(f"tc_N{n_ant}_B{n_beam}_T{n_samp}_Ti{t_int}", P,
+          oracle_power_for_mode(scene, dirs, t_int, mode, X64), mode, tile=q["tile_t"])
+
+
+@pytest.mark.parametrize("tile", [64, 128, 192, 256])
+def test_tc_tile_choices_agree(bf, tile):
+    scene = small_scene(n_ant=32, n_chan=2, n_samp=777)
+    dirs = synth.beam_grid(12, 12)
+    x, X64 = stored_voltages(scene, synth.C16F)
+    P, q = run_power(bf, scene, dirs, 64, synth.C16F, x, tile=tile)
+    assert q["tile_t"] == tile
+    check(f"tc_tile{tile}", P, oracle_power_for_mode(scene, dirs, 64, synth.C16F, X64), synth.C16F)
+
+
+@pytest.mark.parametrize("mode", [synth.C16F, synth.C8E4M3])
+def test_tc_complex_beams(bf, mode):
+    sigma = 16.0 if mode == synth.C8E4M3 else 0.7071
+    scene = small_scene(n_ant=32, n_chan=2, n_samp=300, sigma=sigma)
+    dirs = synth.beam_grid(10, 10)
+    x, X64 = stored_voltages(scene, mode)
+    Wq, _, _ = oracle.quantised_weights(oracle.weights(scene.pos, scene.freqs, dirs), mode)
+    Bref = oracle.beams(Wq, X64)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, mode, 64)
+    Bg = plan.execute_complex(dev(x)).cpu().numpy()
+    plan.close()
+    Bg = Bg[..., 0] + 1j * Bg[..., 1]
+    err = float(np.max(np.abs(Bg - Bref)) / np.max(np.abs(Bref)))
+    record("tc_complex", err, 0.0, mode=synth.MODE_NAMES[mode])
+    assert err < (1e-4 if mode == synth.C8E4M3 else 1e-5)
+
+
+def test_tc_nct_layout_equals_ctn(bf):
+    scene = small_scene(n_ant=32, n_chan=3, n_samp=500)
+    dirs = synth.beam_grid(8, 8)
+    x, _ = stored_voltages(scene, synth.C16F)
+    P1, _ = run_power(bf, scene, dirs, 64, synth.C16F, x)
+    P2, _ = run_power(bf, scene, dirs, 64, synth.C16F, synth.to_nct(x, synth.C16F), layout=bf.BF_LAYOUT_NCT)
+    assert np.array_equal(P1, P2)
+
+
+def test_mask_is_the_sub_array(bf):
+    """Sub-arraying with an antenna mask (Section 3.1) equals a plan built on
+    the unmasked antennas alone, fed only their voltages."""
+    scene = small_scene(n_ant=32, n_chan=2, n_samp=256)
+    dirs = synth.beam_grid(8, 8)
+    mask = np.zeros(32, np.uint8)
+    keep = np.array([0, 3, 5, 8, 9, 12, 20, 21, 22, 30, 31, 2])
+    mask[keep] = 1
+    x, X64 = stored_voltages(scene, synth.C16F)
+    P, _ = run_power(bf, scene, dirs, 64, synth.C16F, x, mask=mask)
+    P_ref = oracle_power_for_mode(scene, dirs, 64, synth.C16F, X64, mask=mask)
+    check("tc_mask", P, P_ref, synth.C16F)
+
+
+def test_input_order_permutation(bf):
+    """Voltages arriving in F-engine order (antenna n in slot perm[n]) give
+    the same powers once the plan knows the order (Section 3)."""
+    scene = small_scene(n_ant=32, n_chan=2, n_samp=256)
+    dirs = synth.beam_grid(8, 8)
+    x, X64 = stored_voltages(scene, synth.C16F)
+    perm = np.random.default_rng(3).permutation(32)
+    xs = np.empty_like(x)
+    xs[:, :, 0::2][:, :, perm] = x[:, :, 0::2]
+    xs[:, :, 1::2][:, :, perm] = x[:, :, 1::2]
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, synth.C16F, 64)
+    P0 = plan.execute(dev(x)).cpu().numpy()
+    plan.set_input_order(perm)
+    P1 = plan.execute(dev(xs)).cpu().numpy()
+    plan.close()
+    assert np.array_equal(P0, P1)
+
+
+@pytest.mark.parametrize("mode", [synth.C32, synth.C16F, synth.C8E4M3, synth.CI8, synth.CI4])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_incoherent(bf, mode, layout):
+    scene = small_scene(n_ant=24, n_chan=3, n_samp=300, sigma=3.0)
+    x, X64 = stored_voltages(scene, mode)
+    mask = np.ones(24, np.uint8)
+    mask[[1, 7]] = 0
+    xin = synth.to_nct(x, mode) if layout else x
+    plan = bf.Plan(scene.pos, scene.freqs, synth.beam_grid(2, 2), mode, 16, layout, mask=mask)
+    P = plan.execute_incoherent(dev(xin)).cpu().numpy()
+    plan.close()
+    ref = oracle.incoherent(X64[:, :, mask == 1], 16)
+    mx, l2 = rel_errors(P, ref)
+    record("incoherent", mx, l2, mode=synth.MODE_NAMES[mode])
+    assert mx < 1e-5
+
+
+# ----------------------------------------------------------------- corner turn
+@pytest.mark.parametrize("mode", [synth.C32, synth.C16F, synth.C8E4M3, synth.CI8, synth.CI4])
+def test_corner_turn_bit_exact(bf, mode):
+    scene = small_scene(n_ant=37, n_chan=3, n_samp=70, sigma=4.0)
+    x = synth.voltages(scene, mode)                  # [c][t][w]
+    nct = synth.to_nct(x, mode)
+    perm = np.random.default_rng(5).permutation(37)
+    out = torch.empty(x.nbytes, dtype=torch.uint8, device="cuda")
+    bf.bf_corner_turn(dev(nct).data_ptr(), mode, out.data_ptr(), mode, 37, 3, 70, perm=perm)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(x.dtype).reshape(x.shape)
+    ref = oracle.corner_turn(nct, perm)                # [c][t][n](,2)
+    assert np.array_equal(got, ref.reshape(x.shape))
+
+
+@pytest.mark.parametrize("mode", [synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8, synth.CI4])
+def test_corner_turn_quantises(bf, mode):
+    scene = small_scene(n_ant=16, n_chan=2, n_samp=90, sigma=6.0)
+    x32 = synth.voltages(scene, synth.C32)
+    nct = synth.to_nct(x32, synth.C32)
+    want = synth.voltages(scene, mode)
+    out = torch.empty(want.nbytes, dtype=torch.uint8, device="cuda")
+    bf.bf_corner_turn(dev(nct).data_ptr(), synth.C32, out.data_ptr(), mode, 16, 2, 90)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(want.dtype).reshape(want.shape)
+    # compare decoded values against the oracle's rounding of the FP32 input
+    vals = oracle.decode_voltages(mode, got)
+    z = x32.view(np.complex64).astype(np.complex128)
+    if mode == synth.CI4:
+        ref = np.clip(np.rint(z.real), -8, 7) + 1j * np.clip(np.rint(z.imag), -8, 7)
+    else:
+        ref = oracle.encode_real(mode, z.real) + 1j * oracle.encode_real(mode, z.imag)
+    assert np.array_equal(vals, ref)
+
+
+# ---------------------------------------------------------- API behaviours
+def test_execute_host_equals_device(bf):
+    scene = small_scene(n_ant=32, n_chan=20, n_samp=512)
+    dirs = synth.beam_grid(8, 8)
+    x, _ = stored_voltages(scene, synth.C16F)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, synth.C16F, 64)
+    Pd = plan.execute(dev(x)).cpu().numpy()
+    Ph = plan.execute_host(torch.from_numpy(x).pin_memory()).numpy()
+    plan.close()
+    assert np.array_equal(Pd, Ph)
+
+
+def test_deterministic(bf):
+    scene = small_scene(n_ant=32, n_chan=4, n_samp=1000)
+    dirs = synth.beam_grid(16, 16)
+    x, _ = stored_voltages(scene, synth.C16F)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, synth.C16F, 64)
+    xd = dev(x)
+    P1 = plan.execute(xd).cpu().numpy()
+    P2 = plan.execute(xd).cpu().numpy()
+    plan.close()
+    assert np.array_equal(P1, P2)
+
+
+def test_tracking_update_equals_fresh_plan(bf):
+    scene = small_scene(n_ant=32, n_chan=2, n_samp=256)
+    d1 = synth.beam_grid(8, 8, 10.0)
+    d2 = synth.beam_grid(8, 8, 4.0)
+    x, _ = stored_voltages(scene, synth.C16F)
+    xd = dev(x)
+    plan = bf.Plan(scene.pos, scene.freqs, d1, synth.C16F, 64)
+    plan.weights(d2)
+    P1 = plan.execute(xd).cpu().numpy()
+    plan.close()
+    fresh = bf.Plan(scene.pos, scene.freqs, d2, synth.C16F, 64)
+    P2 = fresh.execute(xd).cpu().numpy()
+    fresh.close()
+    assert np.array_equal(P1, P2)
+
+
+def test_empty_and_short_inputs(bf):
+    scene = small_scene(n_ant=32, n_chan=2, n_samp=40)
+    dirs = synth.beam_grid(4, 4)
+    x, _ = stored_voltages(scene, synth.C16F)
+    for mode_plan in (synth.C16F,):
+        plan = bf.Plan(scene.pos, scene.freqs, dirs, mode_plan, 64)
+        out = plan.execute(dev(x))          # T = 40 < T_int: no window
+        assert out.shape == (16, 2, 0)
+        out0 = torch.empty(1, device="cuda")
+        bf.bf_execute(plan.handle, dev(x).data_ptr(), 0, out0.data_ptr())
+        plan.sync()
+        plan.close()
+
+
+def test_misaligned_pointer_rejected(bf):
+    scene = small_scene(n_ant=32, n_chan=1, n_samp=64)
+    dirs = synth.beam_grid(2, 2)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, synth.C16F, 64)
+    buf = torch.zeros(64 * 32 * 2 + 8, dtype=torch.float16, device="cuda")
+    out = torch.empty(64, device="cuda")
+    with pytest.raises(bf.BFError) as ei:
+        bf.bf_execute(plan.handle, buf.data_ptr() + 2, 64, out.data_ptr())
+    assert ei.value.status == bf.BF_ERR_ARG
+    plan.close()
+
+
+# ------------------------------------------------------- full-size workload
+@pytest.mark.slow
+def test_config2_full_size_sampled_channels(bf):
+    """The real-time FP16 workload at full size (32 antennas, 1024 channels,
+    1024 beams, 15625 samples, T_int = 64) in the launch configuration the
+    benchmark times; the oracle checks 8 seeded channels in full."""
+    scene, dirs, t_int = synth.config2()
+    x = synth.voltages(scene, synth.C16F)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, synth.C16F, t_int)
+    xd = dev(x)
+    del x
+    P = plan.execute(xd)
+    plan.sync()
+    chans = sorted(np.random.default_rng(2).choice(1024, size=8, replace=False).tolist())
+    Pg = P[:, chans, :].cpu().numpy()
+    plan.close()
+    del xd, P
+    sub = synth.Scene(pos=scene.pos, freqs=scene.freqs, n_samp=scene.n_samp, seed=scene.seed,
+                      noise_sigma=scene.noise_sigma, sources=scene.sources)
+    xs = synth.voltages(sub, synth.C16F, channels=chans)
+    X64 = oracle.decode_voltages(synth.C16F, xs)
+    P_ref = oracle_power_for_mode(sub, dirs, t_int, synth.C16F, X64, channels=chans)
+    check("config2_full_sampled", Pg, P_ref, synth.C16F, channels=chans)
