@@ -56,7 +56,7 @@ static void plan_free(bf_plan *p)
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->stream2) cudaStreamSynchronize(p->stream2);
     if (p->stream3) cudaStreamSynchronize(p->stream3);
-    void *ptrs[] = {p->d_pos, p->d_freqs, p->d_dirs, p->d_mask, p->d_tau, p->d_w, p->d_wscale,
+    void *ptrs[] = {p->d_pos, p->d_freqs, p->d_dirs, p->d_mask, p->d_tau, p->d_ab, p->d_w, p->d_wscale,
                     p->d_wsig, p->d_scratch, p->d_hx, p->d_hp, p->d_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -158,6 +158,12 @@ bf_status bf_plan_create(bf_plan **out, int n_ant, const double *pos_m, const ui
     p->dirs.assign(dirs, dirs + 3 * (size_t)n_beam);
     if (mask) p->mask.assign(mask, mask + n_ant);
     p->kernel = dtype == BF_C32 ? BF_KERNEL_SIMT : BF_KERNEL_TC;
+    // uniformly spaced channels use the exact fixed-point phase recurrence
+    p->f0 = freqs_hz[0];
+    p->df = n_chan > 1 ? (freqs_hz[n_chan - 1] - freqs_hz[0]) / (n_chan - 1) : 0.0;
+    p->uniform_freqs = true;
+    for (int c = 0; c < n_chan; ++c)
+        if (std::fabs(freqs_hz[c] - (p->f0 + c * p->df)) > 1e-6) p->uniform_freqs = false;
 
     std::string why;
     if (!choose_format(p, &why)) {
@@ -182,6 +188,7 @@ bf_status bf_plan_create(bf_plan **out, int n_ant, const double *pos_m, const ui
         {(void **)&p->d_dirs, 3 * (size_t)p->B * sizeof(double)},
         {(void **)&p->d_mask, (size_t)p->N},
         {(void **)&p->d_tau, (size_t)p->N * p->B * sizeof(double)},
+        {(void **)&p->d_ab, (size_t)p->N * p->B * 2 * sizeof(unsigned long long)},
         {(void **)&p->d_w, p->w_bytes},
         {(void **)&p->d_wscale, (size_t)p->C * f.b_pad * sizeof(float)},
         {(void **)&p->d_wsig, (size_t)p->C * f.b_pad * sizeof(float)},

@@ -77,6 +77,9 @@ struct bf_plan {
     double *d_pos = nullptr, *d_freqs = nullptr, *d_dirs = nullptr;
     uint8_t *d_mask = nullptr;
     double *d_tau = nullptr;          // [B][N] geometric delays (s)
+    unsigned long long *d_ab = nullptr;   // [B][N][2] frac(f0 tau), frac(df tau) in 2^-64 cycles
+    bool uniform_freqs = false;       // f_c = f0 + c df within 1 uHz
+    double f0 = 0.0, df = 0.0;
 
     bfi::WeightFormat wf;
     void *d_w = nullptr;              // weights in the format above

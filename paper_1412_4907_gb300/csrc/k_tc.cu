@@ -12,20 +12,25 @@
 // there.
 //
 // Structure (one CTA per SM, persistent):
-//   warp 0      TMA producer: voltage tiles [NT samples x K] double-buffered,
-//               and the weight rows of a group of M tiles kept resident in
-//               shared memory while the CTA walks along time (weights are
-//               reused for every sample, Section 2.1)
-//   warp 1      allocates 512 TMEM columns; one thread issues tcgen05.mma,
-//               128 x NT x 16 (or x32 for FP8) per instruction, into two
-//               NT-column FP32 accumulators (the epilogue drains one while
-//               the next tile accumulates)
-//   warps 2-9   epilogue: tcgen05.ld of the accumulator, squares, window
-//               sums in a fixed order, re+im combination via one shuffle
-//               (the two rows of a beam are 16 lanes apart), store.
-// Work unit = (channel, M-tile group, time tile); each CTA takes a
-// contiguous, equal share of units, so consecutive units share a channel and
-// group and the resident weights are reloaded only when they change.
+//   warp 0       TMA producer: voltage tiles [NT samples x K] double-buffered,
+//                and the weight rows of a group of M tiles kept resident in
+//                shared memory while the CTA walks along time (weights are
+//                reused for every sample, Section 2.1)
+//   warp 1       allocates 512 TMEM columns; one thread issues tcgen05.mma,
+//                128 x NT x 16 (or x32 for FP8) per instruction, into two
+//                NT-column FP32 accumulators (the epilogue drains one while
+//                the next tile accumulates)
+//   warps 2-17   epilogue, four warps per TMEM lane quarter, each on a slice
+//                of the tile's columns: one 64-column tcgen05.ld per wait,
+//                squares, window sums in a fixed order, re+im combination via
+//                one shuffle (the two rows of a beam are 16 lanes apart); the
+//                window powers of a tile are staged in shared memory and one
+//                warp per quarter writes each beam's run as 16-byte stores.
+// Work: the M tiles of a channel are split into weight groups; the CTAs are
+// arranged as P sets of Gq CTAs, the CTAs of one set hold different groups
+// and walk the same (channel, time-tile) range in step, so a voltage tile is
+// read from DRAM once and served to the other group's CTA from L2.  Weights
+// are reloaded only when the channel changes.
 // Every wait is bounded (2 s); a timeout raises the plan's error word, all
 // roles leave their loops, in-flight copies and MMAs are drained and TMEM is
 // freed before the CTA exits.
@@ -39,15 +44,17 @@
 
 namespace bfi {
 
-constexpr int kTcThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kTcThreads = (2 + kEpiWarps) * 32;
 constexpr int kTmemCols = 512;
+constexpr int kMaxWinPerTile = 16;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 
 struct TcKernelArgs {
-    long long units;
-    int n_groups, g_base, g_rem, gmax;
-    int t_tiles, nt, kb, ke, nsplit;
+    long long ct_total;                 // channels x time tiles
+    int n_groups, g_base, g_rem, gmax;  // weight groups of M tiles
+    int gq;                             // CTAs per set (distinct groups walked in step)
+    int t_tiles, nt, kb, ke, nsplit, wpt;
     int c_base, c_total, T, T_o, t_int, B, b_pad;
     uint32_t idesc;
     uint32_t x_stage_bytes, w_slot_bytes;
@@ -57,27 +64,15 @@ struct TcKernelArgs {
     unsigned *err;
 };
 
-struct Unit {
-    int c, g, tt, m0, gs;
-    long long cg;
-};
-
-__device__ __forceinline__ Unit decode_unit(const TcKernelArgs &a, long long u)
+__device__ __forceinline__ void group_tiles(const TcKernelArgs &a, int g, int &m0, int &gs)
 {
-    Unit r;
-    r.tt = (int)(u % a.t_tiles);
-    long long q = u / a.t_tiles;
-    r.g = (int)(q % a.n_groups);
-    r.c = (int)(q / a.n_groups);
-    r.cg = q;
-    if (r.g < a.g_rem) {
-        r.gs = a.g_base + 1;
-        r.m0 = r.g * (a.g_base + 1);
+    if (g < a.g_rem) {
+        gs = a.g_base + 1;
+        m0 = g * (a.g_base + 1);
     } else {
-        r.gs = a.g_base;
-        r.m0 = a.g_rem * (a.g_base + 1) + (r.g - a.g_rem) * a.g_base;
+        gs = a.g_base;
+        m0 = a.g_rem * (a.g_base + 1) + (g - a.g_rem) * a.g_base;
     }
-    return r;
 }
 
 // Bounded wait that ignores the abort flag (used only to drain on abort).
@@ -88,8 +83,22 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity)
         if (global_ns() - t0 > 200000000ull) break;   // 0.2 s
 }
 
+// Sum of squares of 16 values with four independent chains.
+__device__ __forceinline__ float sumsq16(const float *v)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+        s0 = fmaf(v[i], v[i], s0);
+        s1 = fmaf(v[i + 1], v[i + 1], s1);
+        s2 = fmaf(v[i + 2], v[i + 2], s2);
+        s3 = fmaf(v[i + 3], v[i + 3], s3);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
 template <bool F8, bool FASTWIN, bool COMPLEX>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __maxnreg__(112)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -98,7 +107,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t sx = base;
     const uint32_t sw = sx + 2 * a.x_stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + 2 * a.x_stage_bytes + a.gmax * a.w_slot_bytes);
+    float *stage = reinterpret_cast<float *>(gbase + 2 * a.x_stage_bytes + a.gmax * a.w_slot_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * kBeamsPerMTile * kMaxWinPerTile);
     const uint32_t b_xfull = smem_u32(bars + 0);
     const uint32_t b_xempty = smem_u32(bars + 2);
     const uint32_t b_tfull = smem_u32(bars + 4);
@@ -106,7 +116,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t b_drain = smem_u32(bars + 8);
     const uint32_t b_wfull = smem_u32(bars + 9);
     const uint32_t b_wempty = smem_u32(bars + 9 + a.gmax);
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 9 + 2 * a.gmax);
+    const uint32_t b_sfull = smem_u32(bars + 9 + 2 * a.gmax);   // [acc][quarter]: slices staged
+    const uint32_t b_sempty = b_sfull + 8 * 8;                   // [acc][quarter]: staging read out
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 9 + 2 * a.gmax + 16);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -124,6 +136,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(b_wfull + 8 * s, 1);
             mbar_init(b_wempty + 8 * s, 1);
         }
+        for (int i = 0; i < 8; ++i) {
+            mbar_init(b_sfull + 8 * i, a.nsplit);
+            mbar_init(b_sempty + 8 * i, 1);
+        }
         *abort_flag = 0;
         fence_mbar_init();
         prefetch_tensormap(&xmap);
@@ -135,43 +151,56 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    const long long u0 = a.units * blockIdx.x / gridDim.x;
-    const long long u1 = a.units * (blockIdx.x + 1) / gridDim.x;
+    // this CTA: groups gq0, gq0 + gq, ...; (channel, time-tile) range of its set
+    const int gq0 = blockIdx.x % a.gq;
+    const int set = blockIdx.x / a.gq;
+    const int n_sets = gridDim.x / a.gq;
+    const long long ct0 = a.ct_total * set / n_sets;
+    const long long ct1 = a.ct_total * (set + 1) / n_sets;
+    const int c_first = (int)(ct0 / a.t_tiles), tt_first = (int)(ct0 % a.t_tiles);
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t xcnt = 0, wcnt = 0, x_issued = 0, w_issued = 0;
             int xs = 0;
-            long long prev = -1;
-            for (long long u = u0; u < u1; ++u) {
-                const Unit w = decode_unit(a, u);
-                if (!mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitNs))
-                    break;
-                xcnt ^= 1u << xs;
-                x_issued |= 1u << xs;
-                mbar_arrive_expect_tx(b_xfull + 8 * xs, a.x_stage_bytes);
-                for (int kb = 0; kb < a.kb; ++kb)
-                    tma_load_3d(sx + xs * a.x_stage_bytes + kb * a.nt * 128, &xmap, b_xfull + 8 * xs,
-                                kb * a.ke, w.tt * a.nt, w.c);
-                xs ^= 1;
-                if (w.cg != prev) {
-                    bool ok = true;
-                    for (int s = 0; s < w.gs; ++s) {
-                        if (!mbar_wait(b_wempty + 8 * s, ((wcnt >> s) & 1u) ^ 1u, abort_flag, a.err,
-                                       kWaitLimitNs)) {
-                            ok = false;
-                            break;
-                        }
-                        wcnt ^= 1u << s;
-                        w_issued |= 1u << s;
-                        mbar_arrive_expect_tx(b_wfull + 8 * s, a.w_slot_bytes);
-                        for (int kb = 0; kb < a.kb; ++kb)
-                            tma_load_3d(sw + s * a.w_slot_bytes + kb * 16384, &wmap, b_wfull + 8 * s,
-                                        kb * a.ke, (w.m0 + s) * kRowsPerMTile, a.c_base + w.c);
+            bool ok = true;
+            for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+                int m0, gs;
+                group_tiles(a, g, m0, gs);
+                int c = c_first, tt = tt_first;
+                for (long long ct = ct0; ct < ct1; ++ct) {
+                    if (!mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitNs)) {
+                        ok = false;
+                        break;
                     }
-                    if (!ok) break;
-                    prev = w.cg;
+                    xcnt ^= 1u << xs;
+                    x_issued |= 1u << xs;
+                    mbar_arrive_expect_tx(b_xfull + 8 * xs, a.x_stage_bytes);
+                    for (int kb = 0; kb < a.kb; ++kb)
+                        tma_load_3d(sx + xs * a.x_stage_bytes + kb * a.nt * 128, &xmap, b_xfull + 8 * xs,
+                                    kb * a.ke, tt * a.nt, c);
+                    xs ^= 1;
+                    if (ct == ct0 || tt == 0) {   // weights of (group, channel)
+                        for (int s = 0; s < gs; ++s) {
+                            if (!mbar_wait(b_wempty + 8 * s, ((wcnt >> s) & 1u) ^ 1u, abort_flag, a.err,
+                                           kWaitLimitNs)) {
+                                ok = false;
+                                break;
+                            }
+                            wcnt ^= 1u << s;
+                            w_issued |= 1u << s;
+                            mbar_arrive_expect_tx(b_wfull + 8 * s, a.w_slot_bytes);
+                            for (int kb = 0; kb < a.kb; ++kb)
+                                tma_load_3d(sw + s * a.w_slot_bytes + kb * 16384, &wmap, b_wfull + 8 * s,
+                                            kb * a.ke, (m0 + s) * kRowsPerMTile, a.c_base + c);
+                        }
+                        if (!ok) break;
+                    }
+                    if (++tt == a.t_tiles) {
+                        tt = 0;
+                        ++c;
+                    }
                 }
             }
             if (*abort_flag) {   // let every issued copy land before the CTA exits
@@ -187,46 +216,53 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) {
             uint32_t xpar = 0, wpar = 0, tpar = 0;
             int xs = 0, acc = 0;
-            long long prev = -1;
-            const int ksteps = 4;   // 32-byte K steps per 128-byte block
-            for (long long u = u0; u < u1; ++u) {
-                const Unit w = decode_unit(a, u);
-                const bool newg = w.cg != prev;
-                prev = w.cg;
-                const bool lastg = (u + 1 == u1) || decode_unit(a, u + 1).cg != w.cg;
-                if (!mbar_wait(b_xfull + 8 * xs, (xpar >> xs) & 1u, abort_flag, a.err, kWaitLimitNs)) break;
-                xpar ^= 1u << xs;
-                bool ok = true;
-                for (int s = 0; s < w.gs; ++s) {
-                    if (newg) {
-                        if (!mbar_wait(b_wfull + 8 * s, (wpar >> s) & 1u, abort_flag, a.err, kWaitLimitNs)) {
-                            ok = false;
-                            break;
-                        }
-                        wpar ^= 1u << s;
-                    }
-                    if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err,
-                                   kWaitLimitNs)) {
+            bool ok = true;
+            for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+                int m0, gs;
+                group_tiles(a, g, m0, gs);
+                (void)m0;
+                int tt = tt_first;
+                for (long long ct = ct0; ct < ct1 && ok; ++ct) {
+                    const bool neww = (ct == ct0) || tt == 0;
+                    const bool lastw = (ct + 1 == ct1) || tt + 1 == a.t_tiles;
+                    if (!mbar_wait(b_xfull + 8 * xs, (xpar >> xs) & 1u, abort_flag, a.err, kWaitLimitNs)) {
                         ok = false;
                         break;
                     }
-                    tpar ^= 1u << acc;
-                    tc_fence_after();
-                    const uint32_t d = tmem + acc * a.nt;
-                    for (int kb = 0; kb < a.kb; ++kb)
-                        for (int ks = 0; ks < ksteps; ++ks) {
-                            const uint64_t ad = sdesc_sw128(sw + s * a.w_slot_bytes + kb * 16384 + ks * 32);
-                            const uint64_t bd = sdesc_sw128(sx + xs * a.x_stage_bytes + kb * a.nt * 128 + ks * 32);
-                            if (F8) mma_f8(d, ad, bd, a.idesc, (kb | ks) != 0);
-                            else mma_f16(d, ad, bd, a.idesc, (kb | ks) != 0);
+                    xpar ^= 1u << xs;
+                    for (int s = 0; s < gs; ++s) {
+                        if (neww) {
+                            if (!mbar_wait(b_wfull + 8 * s, (wpar >> s) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                                ok = false;
+                                break;
+                            }
+                            wpar ^= 1u << s;
                         }
-                    mma_commit(b_tfull + 8 * acc);
-                    if (lastg) mma_commit(b_wempty + 8 * s);
-                    acc ^= 1;
+                        if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err,
+                                       kWaitLimitNs)) {
+                            ok = false;
+                            break;
+                        }
+                        tpar ^= 1u << acc;
+                        tc_fence_after();
+                        const uint32_t d = tmem + acc * a.nt;
+                        for (int kb = 0; kb < a.kb; ++kb)
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {   // 32-byte K steps per 128-byte block
+                                const uint64_t ad = sdesc_sw128(sw + s * a.w_slot_bytes + kb * 16384 + ks * 32);
+                                const uint64_t bd = sdesc_sw128(sx + xs * a.x_stage_bytes + kb * a.nt * 128 + ks * 32);
+                                if (F8) mma_f8(d, ad, bd, a.idesc, (kb | ks) != 0);
+                                else mma_f16(d, ad, bd, a.idesc, (kb | ks) != 0);
+                            }
+                        mma_commit(b_tfull + 8 * acc);
+                        if (lastw) mma_commit(b_wempty + 8 * s);
+                        acc ^= 1;
+                    }
+                    if (!ok) break;
+                    mma_commit(b_xempty + 8 * xs);
+                    xs ^= 1;
+                    if (++tt == a.t_tiles) tt = 0;
                 }
-                if (!ok) break;
-                mma_commit(b_xempty + 8 * xs);
-                xs ^= 1;
             }
             mma_commit(b_drain);   // all issued MMAs complete before teardown
             drain_wait(b_drain, 0);
@@ -236,106 +272,182 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // -------------------------------------------------------------- epilogue
         const int e = warp - 2;
         const int q = warp & 3;               // TMEM lane quarter this warp may access
-        const int h = e >> 2;                 // column half
+        const int h = e >> 2;                 // column slice
         const int part = (lane >> 4) & 1;     // 0: re row, 1: im row
-        const int bi = q * 16 + (lane & 15);  // beam within the M tile
+        const int bq = q * 16 + (lane & 15);  // beam within the M tile
         const int cols = a.nt / a.nsplit;
         const int col0 = h * cols;
-        uint32_t tpar = 0;
+        const bool active = h < a.nsplit;
+        const int wps = COMPLEX ? 0 : cols / a.t_int;   // windows per slice
+        uint32_t tpar = 0, spar = 0, epar = 0;
         int acc = 0;
-        for (long long u = u0; u < u1; ++u) {
-            const Unit w = decode_unit(a, u);
-            bool ok = true;
-            for (int s = 0; s < w.gs; ++s) {
-                if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitNs)) {
-                    ok = false;
-                    break;
-                }
-                tpar ^= 1u << acc;
-                tc_fence_after();
-                if (h < a.nsplit) {
-                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
-                    const int b = (w.m0 + s) * kBeamsPerMTile + bi;
-                    const int cg = a.c_base + w.c;
-                    const bool bvalid = b < a.B;
-                    if (COMPLEX) {
-                        const float sg = bvalid ? a.wsig[(size_t)cg * a.b_pad + b] : 0.f;
-                        float2 *o2 = reinterpret_cast<float2 *>(a.out);
-                        const size_t ob = ((size_t)b * a.c_total + cg) * a.T;
-                        for (int ch = 0; ch < cols / 16; ++ch) {
-                            float v[16], o[16];
-                            tmem_ld16(taddr + ch * 16, v);
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 16);
-                            const int t0 = w.tt * a.nt + col0 + ch * 16;
-                            // lanes 0-15 hold the re row and store samples 0-7 of the
-                            // chunk; lanes 16-31 hold the im row and store samples 8-15
-                            if (bvalid && part == 0) {
-#pragma unroll
-                                for (int i = 0; i < 8; ++i)
-                                    if (t0 + i < a.T) o2[ob + t0 + i] = make_float2(v[i] * sg, o[i] * sg);
-                            } else if (bvalid) {
-#pragma unroll
-                                for (int i = 8; i < 16; ++i)
-                                    if (t0 + i < a.T) o2[ob + t0 + i] = make_float2(o[i] * sg, v[i] * sg);
-                            }
+        bool ok = true;
+        for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+            int m0, gs;
+            group_tiles(a, g, m0, gs);
+            int c = c_first, tt = tt_first;
+            for (long long ct = ct0; ct < ct1 && ok; ++ct) {
+                const int cg = a.c_base + c;
+                for (int s = 0; s < gs; ++s) {
+                    if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    tpar ^= 1u << acc;
+                    const uint32_t sfull = b_sfull + 8 * (acc * 4 + q), sempty = b_sempty + 8 * (acc * 4 + q);
+                    if (!COMPLEX && active) {
+                        // the staging buffer of this accumulator is free once the previous
+                        // tile that used it has been written out
+                        if (!mbar_wait(sempty, ((epar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitNs)) {
+                            ok = false;
+                            break;
                         }
-                    } else {
-                        const float scale = bvalid ? a.wscale[(size_t)cg * a.b_pad + b] : 0.f;
-                        const int nw = cols / a.t_int;
-                        const int j_base = (w.tt * a.nt + col0) / a.t_int;
-                        float *orow = a.out + ((size_t)b * a.c_total + cg) * a.T_o;
-                        if (FASTWIN) {
-                            const int nch = a.t_int / 16;
-                            for (int wi = 0; wi < nw; ++wi) {
-                                float ws = 0.f;
-                                for (int ch = 0; ch < nch; ++ch) {
-                                    float v[16];
-                                    tmem_ld16(taddr + wi * a.t_int + ch * 16, v);
-                                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-                                    for (int i = 0; i < 16; i += 4) {
-                                        s0 = fmaf(v[i], v[i], s0);
-                                        s1 = fmaf(v[i + 1], v[i + 1], s1);
-                                        s2 = fmaf(v[i + 2], v[i + 2], s2);
-                                        s3 = fmaf(v[i + 3], v[i + 3], s3);
-                                    }
-                                    ws += (s0 + s1) + (s2 + s3);
-                                }
-                                const float pw = (ws + __shfl_xor_sync(0xffffffffu, ws, 16)) * scale;
-                                const int j = j_base + wi;
-                                const bool mine = (nw == 1) ? (part == 0) : ((wi & 1) == part);
-                                if (mine && bvalid && j < a.T_o) orow[j] = pw;
-                            }
-                        } else {
-                            float ws = 0.f;
-                            int cnt = 0, wi = 0;
+                        epar ^= 1u << acc;
+                    }
+                    tc_fence_after();
+                    const int b_tile0 = (m0 + s) * kBeamsPerMTile;
+                    const int b = b_tile0 + bq;
+                    const bool bvalid = b < a.B;
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
+                    float *stg = stage + acc * (kBeamsPerMTile * kMaxWinPerTile);
+                    if (COMPLEX) {
+                        if (active) {
+                            const float sg = bvalid ? a.wsig[(size_t)cg * a.b_pad + b] : 0.f;
+                            float2 *o2 = reinterpret_cast<float2 *>(a.out);
+                            const size_t ob = ((size_t)b * a.c_total + cg) * a.T;
                             for (int ch = 0; ch < cols / 16; ++ch) {
-                                float v[16];
+                                float v[16], o[16];
                                 tmem_ld16(taddr + ch * 16, v);
 #pragma unroll
-                                for (int i = 0; i < 16; ++i) {
-                                    ws = fmaf(v[i], v[i], ws);
-                                    if (++cnt == a.t_int) {
-                                        const float pw = (ws + __shfl_xor_sync(0xffffffffu, ws, 16)) * scale;
-                                        const int j = j_base + wi;
-                                        const bool mine = (nw == 1) ? (part == 0) : ((wi & 1) == part);
-                                        if (mine && bvalid && j < a.T_o) orow[j] = pw;
+                                for (int i = 0; i < 16; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 16);
+                                const int t0 = tt * a.nt + col0 + ch * 16;
+                                // lanes 0-15 hold the re row and store samples 0-7 of the
+                                // chunk; lanes 16-31 hold the im row and store samples 8-15
+                                if (bvalid && part == 0) {
+#pragma unroll
+                                    for (int i = 0; i < 8; ++i)
+                                        if (t0 + i < a.T) o2[ob + t0 + i] = make_float2(v[i] * sg, o[i] * sg);
+                                } else if (bvalid) {
+#pragma unroll
+                                    for (int i = 8; i < 16; ++i)
+                                        if (t0 + i < a.T) o2[ob + t0 + i] = make_float2(o[i] * sg, v[i] * sg);
+                                }
+                            }
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
+                    } else {
+                        if (active) {
+                            const float scale = bvalid ? a.wscale[(size_t)cg * a.b_pad + b] : 0.f;
+                            float ws = 0.f;
+                            int wi = 0, cnt = 0;
+                            auto emit = [&](float sum) {
+                                const float pw = (sum + __shfl_xor_sync(0xffffffffu, sum, 16)) * scale;
+                                if (part == 0) stg[bq * kMaxWinPerTile + h * wps + wi] = pw;
+                                ++wi;
+                            };
+                            int col = 0;
+                            for (; col + 64 <= cols; col += 64) {
+                                float v[64];
+                                tmem_ld64(taddr + col, v);
+                                if (FASTWIN) {
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) {
+                                        ws += sumsq16(v + 16 * k);
+                                        cnt += 16;
+                                        if (cnt == a.t_int) {
+                                            emit(ws);
+                                            ws = 0.f;
+                                            cnt = 0;
+                                        }
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int i = 0; i < 64; ++i) {
+                                        ws = fmaf(v[i], v[i], ws);
+                                        if (++cnt == a.t_int) {
+                                            emit(ws);
+                                            ws = 0.f;
+                                            cnt = 0;
+                                        }
+                                    }
+                                }
+                            }
+                            for (; col < cols; col += 16) {
+                                float v[16];
+                                tmem_ld16(taddr + col, v);
+                                if (FASTWIN) {
+                                    ws += sumsq16(v);
+                                    cnt += 16;
+                                    if (cnt == a.t_int) {
+                                        emit(ws);
                                         ws = 0.f;
                                         cnt = 0;
-                                        ++wi;
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int i = 0; i < 16; ++i) {
+                                        ws = fmaf(v[i], v[i], ws);
+                                        if (++cnt == a.t_int) {
+                                            emit(ws);
+                                            ws = 0.f;
+                                            cnt = 0;
+                                        }
                                     }
                                 }
                             }
                         }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(b_tempty + 8 * acc);
+                            if (active) mbar_arrive(sfull);
+                        }
+                        if (active && h == 0) {
+                            // the slices of this quarter are staged: one warp writes each
+                            // beam's run of windows with vector stores
+                            if (!mbar_wait(sfull, (spar >> acc) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                                ok = false;
+                                break;
+                            }
+                            spar ^= 1u << acc;
+                            {
+                                const int j0 = tt * a.wpt;
+                                const int nj = min(a.wpt, a.T_o - j0);
+                                if ((a.T_o & 3) == 0 && (a.wpt & 3) == 0) {
+                                    const int per = a.wpt >> 2;
+                                    for (int i = lane; i < 16 * per; i += 32) {
+                                        const int bl = i / per, k = (i % per) * 4;
+                                        const int bb = b_tile0 + q * 16 + bl;
+                                        if (bb < a.B && k < nj) {
+                                            const float4 v4 = *reinterpret_cast<const float4 *>(
+                                                stg + (q * 16 + bl) * kMaxWinPerTile + k);
+                                            *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o +
+                                                                        j0 + k) = v4;
+                                        }
+                                    }
+                                } else {
+                                    for (int i = lane; i < 16 * a.wpt; i += 32) {
+                                        const int bl = i / a.wpt, k = i % a.wpt;
+                                        const int bb = b_tile0 + q * 16 + bl;
+                                        if (bb < a.B && k < nj)
+                                            a.out[((size_t)bb * a.c_total + cg) * a.T_o + j0 + k] =
+                                                stg[(q * 16 + bl) * kMaxWinPerTile + k];
+                                    }
+                                }
+                            }
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(sempty);
+                        }
                     }
+                    acc ^= 1;
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
-                acc ^= 1;
+                if (++tt == a.t_tiles) {
+                    tt = 0;
+                    ++c;
+                }
             }
-            if (!ok) break;
         }
     }
 
@@ -373,6 +485,9 @@ static int gcd_i(int x, int y)
     return x;
 }
 
+static int ctrl_bytes() { return 8 * (9 + 2 * 16 + 16) + 16; }
+static int stage_bytes() { return 2 * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
+
 bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
 {
     const WeightFormat &f = p->wf;
@@ -386,20 +501,28 @@ bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
     for (int nt = 256; nt >= (int)unit; nt -= 16) {
         if (nt % unit) continue;
         if (tile_req && nt != tile_req) continue;
+        if (nt / t_int > kMaxWinPerTile) continue;   // staged window powers per tile
         TcConfig c;
         c.nt = nt;
-        c.nsplit = ((nt / 2) % t_int == 0 && (nt / 2) % 16 == 0) ? 2 : 1;
+        c.nsplit = 1;
+        for (int ns : {4, 2}) {
+            const int w = nt / ns;
+            if (nt % ns == 0 && w % 16 == 0 && w % t_int == 0) {
+                c.nsplit = ns;
+                break;
+            }
+        }
         c.fast_windows = (t_int % 16) == 0;
         const int x_stage = f.kb * nt * 128;
         const int w_slot = f.kb * 16384;
-        const int ctrl = 8 * (9 + 2 * 16) + 16;
-        const int avail = kSmemLimit - 2 * x_stage - ctrl - 1024;
+        const int fixed = 2 * x_stage + stage_bytes() + ctrl_bytes() + 1024;
+        const int avail = kSmemLimit - fixed;
         if (avail < w_slot) continue;
         int g = std::min(mt, std::min(16, avail / w_slot));
         c.n_groups = (mt + g - 1) / g;
         const int g_base = mt / c.n_groups, g_rem = mt % c.n_groups;
         c.group = g_base + (g_rem ? 1 : 0);
-        c.smem = 2 * x_stage + c.group * w_slot + ctrl + 1024;
+        c.smem = fixed + c.group * w_slot;
         c.smem = std::max(c.smem, 116 * 1024);   // one CTA per SM: it owns all 512 TMEM columns
         *cfg = c;
         return true;
@@ -465,11 +588,12 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.g_rem = mt % cfg.n_groups;
     ka.gmax = cfg.group;
     ka.t_tiles = (ta.T + cfg.nt - 1) / cfg.nt;
-    ka.units = (long long)ta.c_launch * cfg.n_groups * ka.t_tiles;
+    ka.ct_total = (long long)ta.c_launch * ka.t_tiles;
     ka.nt = cfg.nt;
     ka.kb = f.kb;
     ka.ke = f.ke;
     ka.nsplit = cfg.nsplit;
+    ka.wpt = cfg.nt / ta.t_int;
     ka.c_base = ta.c_base;
     ka.c_total = ta.c_total;
     ka.T = ta.T;
@@ -486,8 +610,11 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
     ka.err = p->d_err;
-    if (ka.units == 0) return cudaSuccess;
-    const int grid = (int)std::min<long long>(p->num_sms, ka.units);
+    if (ka.ct_total == 0) return cudaSuccess;
+    // sets of gq CTAs hold different weight groups and walk the same range in step
+    ka.gq = std::min(cfg.n_groups, p->num_sms);
+    const long long n_sets = std::max<long long>(1, std::min<long long>(p->num_sms / ka.gq, ka.ct_total));
+    const int grid = (int)(n_sets * ka.gq);
     const bool f8 = f.op == kOpE4M3;
     const bool fw = cfg.fast_windows;
     if (ta.complex_out) {

@@ -1,11 +1,18 @@
 // Weight generation (Eq. 1): W[c][b][n] = exp(-i 2 pi f_c (r_n . s_b) / c0).
 //
-// The phase in cycles, f_c * tau[b][n] with tau = (r_n . s_b) / c0, is formed
-// and reduced to [-1/2, 1/2] in FP64: a 200 m baseline at 416 MHz spans ~277
-// cycles, and FP32 would keep only ~1.7e-5 cycle of the fraction.  The
-// reduced phase is exact in FP32 to 2^-25 cycle, so sin/cos are taken in
-// FP32 (sincospif).  The weights are computed once per plan or pointing
-// update and reused for every sample of every chunk (Section 2.1).
+// The phase in cycles, f_c * tau[b][n] with tau = (r_n . s_b) / c0, is
+// reduced modulo one cycle before sin/cos: a 200 m baseline at 416 MHz spans
+// ~277 cycles, and FP32 would keep only ~1.7e-5 cycle of the fraction.
+// Two exact ways of doing the reduction:
+//  - any channel list: per weight, f_c * tau and its fractional part in FP64;
+//  - uniformly spaced channels f_c = f_0 + c df (checked on the host to
+//    1 uHz): per (beam, antenna), alpha = frac(f_0 tau) and beta =
+//    frac(df tau) are formed in FP64 and kept as 64-bit fixed-point
+//    fractions of a cycle; the phase of channel c is alpha + c beta modulo
+//    2^64, exact in integer arithmetic, so no per-weight FP64 work remains.
+// The reduced phase is then exact in FP32 to 2^-25 cycle and sin/cos are
+// taken in FP32 (sincospif).  The weights are computed once per plan or
+// pointing update and reused for every sample of every chunk (Section 2.1).
 //
 // Tensor-core storage: each beam owns two operand rows of K = 2N real
 // elements against voltages stored as interleaved (Re X, Im X) pairs:
@@ -23,35 +30,74 @@
 namespace bfi {
 
 __global__ void k_delays(const double *__restrict__ pos, const double *__restrict__ dirs, int N, int B,
-                         double *__restrict__ tau)
+                         double f0, double df, double *__restrict__ tau, unsigned long long *__restrict__ ab)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * B) return;
     int b = i / N, n = i % N;
     double rs = pos[3 * n] * dirs[3 * b] + pos[3 * n + 1] * dirs[3 * b + 1] + pos[3 * n + 2] * dirs[3 * b + 2];
-    tau[i] = rs / kC0;
+    double t = rs / kC0;
+    tau[i] = t;
+    // fractional cycles as 64-bit fixed point (2^64 = one cycle)
+    const double two64 = 18446744073709551616.0;
+    double a = f0 * t, d = df * t;
+    a -= floor(a);
+    d -= floor(d);
+    ab[2 * i] = __double2ull_rz(a * two64);
+    ab[2 * i + 1] = __double2ull_rz(d * two64);
 }
 
-__device__ __forceinline__ float2 weight_at(double f, const double *__restrict__ tau, const uint8_t *mask,
-                                            int b, int n, int N, int B)
+// Phase source of one channel: per-weight FP64 (any channel list) or the
+// fixed-point recurrence (uniform channels).
+template <bool FIXED>
+struct Phase {
+    const double *tau;
+    const unsigned long long *ab;
+    double f;
+    unsigned long long c;
+    int N;
+
+    // twice the reduced phase, in [-1, 1], rounded to FP32
+    __device__ __forceinline__ float x32(int b, int n) const
+    {
+        if (FIXED) {
+            const size_t i = (size_t)b * N + n;
+            const unsigned long long ph = ab[2 * i] + c * ab[2 * i + 1];   // modulo 2^64
+            return (float)(int)(ph >> 32) * 4.656612873077393e-10f;        // x 2^-31
+        }
+        double ph = f * tau[(size_t)b * N + n];   // cycles
+        double r = ph - rint(ph);                 // [-1/2, 1/2]
+        return static_cast<float>(2.0 * r);
+    }
+    __device__ __forceinline__ double x64(int b, int n) const
+    {
+        if (FIXED) {
+            const size_t i = (size_t)b * N + n;
+            const unsigned long long ph = ab[2 * i] + c * ab[2 * i + 1];
+            return (double)(long long)ph * 1.0842021724855044e-19;        // x 2^-63
+        }
+        double ph = f * tau[(size_t)b * N + n];
+        return 2.0 * (ph - rint(ph));
+    }
+};
+
+template <bool FIXED>
+__device__ __forceinline__ float2 weight_at(const Phase<FIXED> &ph, const uint8_t *mask, int b, int n, int N, int B)
 {
     if (b >= B || n >= N || (mask && !mask[n])) return make_float2(0.f, 0.f);
-    double ph = f * tau[(size_t)b * N + n];     // cycles
-    double r = ph - rint(ph);                   // [-1/2, 1/2]
     float s, c;
-    sincospif(static_cast<float>(2.0 * r), &s, &c);
-    return make_float2(c, -s);                  // exp(-i 2 pi ph)
+    sincospif(ph.x32(b, n), &s, &c);
+    return make_float2(c, -s);   // exp(-i 2 pi phase)
 }
 
 // The same weight with sin/cos in FP64 (used only near rounding boundaries).
-__device__ __forceinline__ double2 weight_at64(double f, const double *__restrict__ tau, const uint8_t *mask,
-                                               int b, int n, int N, int B)
+template <bool FIXED>
+__device__ __forceinline__ double2 weight_at64(const Phase<FIXED> &ph, const uint8_t *mask, int b, int n, int N,
+                                               int B)
 {
     if (b >= B || n >= N || (mask && !mask[n])) return make_double2(0.0, 0.0);
-    double ph = f * tau[(size_t)b * N + n];
-    double r = ph - rint(ph);
     double s, c;
-    sincospi(2.0 * r, &s, &c);
+    sincospi(ph.x64(b, n), &s, &c);
     return make_double2(c, -s);
 }
 
@@ -103,22 +149,23 @@ __device__ __forceinline__ bool same_value(typename Q::T a, typename Q::T b)
 }
 
 // One warp per (channel, beam slot).
-template <int FMT>
+template <bool FIXED>
 __global__ void k_weights_simt(const double *__restrict__ freqs, const double *__restrict__ tau,
-                               const uint8_t *__restrict__ mask, int N, int B, int b_pad, float2 *__restrict__ w,
-                               float *__restrict__ wscale, float *__restrict__ wsig)
+                               const unsigned long long *__restrict__ ab, const uint8_t *__restrict__ mask, int N,
+                               int B, int b_pad, float2 *__restrict__ w, float *__restrict__ wscale,
+                               float *__restrict__ wsig)
 {
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int c = blockIdx.y;
     if (b >= b_pad) return;
-    const double f = freqs[c];
+    const Phase<FIXED> ph{tau, ab, freqs[c], (unsigned long long)c, N};
     if (lane == 0) {
         wscale[(size_t)c * b_pad + b] = 1.f;
         wsig[(size_t)c * b_pad + b] = 1.f;
     }
     float2 *row = w + ((size_t)c * b_pad + b) * N;
-    for (int n = lane; n < N; n += 32) row[n] = weight_at(f, tau, mask, b, n, N, B);
+    for (int n = lane; n < N; n += 32) row[n] = weight_at(ph, mask, b, n, N, B);
 }
 
 // Tensor-core rows.  Each stored component is first rounded from the FP32
@@ -127,10 +174,11 @@ __global__ void k_weights_simt(const double *__restrict__ freqs, const double *_
 // the whole beam (scaled formats, whose scale depends on every antenna) is
 // recomputed in FP64 and rounded once from double, so the stored value is
 // the format's rounding of the exact weight.
-template <int FMT>
+template <int FMT, bool FIXED>
 __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__restrict__ tau,
-                             const uint8_t *__restrict__ mask, int N, int B, int b_pad, int k_pad,
-                             void *__restrict__ w, float *__restrict__ wscale, float *__restrict__ wsig)
+                             const unsigned long long *__restrict__ ab, const uint8_t *__restrict__ mask, int N,
+                             int B, int b_pad, int k_pad, void *__restrict__ w, float *__restrict__ wscale,
+                             float *__restrict__ wsig)
 {
     using Q = Quant<FMT>;
     using T = typename Q::T;
@@ -139,14 +187,14 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int c = blockIdx.y;
     if (b >= b_pad) return;
-    const double f = freqs[c];
+    const Phase<FIXED> ph{tau, ab, freqs[c], (unsigned long long)c, N};
     const int n_cols = k_pad / 2;
 
     float sig = 1.f;
     if (scaled) {
         float mx = 0.f;
         for (int n = lane; n < N; n += 32) {
-            float2 v = weight_at(f, tau, mask, b, n, N, B);
+            float2 v = weight_at(ph, mask, b, n, N, B);
             mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
 #pragma unroll
@@ -168,7 +216,7 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
     };
     bool redo = false;
     for (int n = lane; n < n_cols; n += 32) {
-        float2 v = weight_at(f, tau, mask, b, n, N, B);
+        float2 v = weight_at(ph, mask, b, n, N, B);
         if (v.x == 0.f && v.y == 0.f) {   // masked antenna, padding beam or padding column
             put(n, T(0), T(0), T(0));
             continue;
@@ -178,7 +226,7 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
         const bool near = !same_value<Q>(Q::q(re - dre), Q::q(re + dre)) ||
                           !same_value<Q>(Q::q(im - dim), Q::q(im + dim));
         if (near && !scaled) {
-            double2 d = weight_at64(f, tau, mask, b, n, N, B);
+            double2 d = weight_at64(ph, mask, b, n, N, B);
             put(n, Q::q(d.x), Q::q(d.y), Q::q(-d.y));
         } else {
             put(n, Q::q(re), Q::q(im), Q::q(-im));
@@ -188,14 +236,14 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
     if (scaled && __any_sync(0xffffffffu, redo)) {
         double mx = 0.0;
         for (int n = lane; n < N; n += 32) {
-            double2 d = weight_at64(f, tau, mask, b, n, N, B);
+            double2 d = weight_at64(ph, mask, b, n, N, B);
             mx = fmax(mx, fmax(fabs(d.x), fabs(d.y)));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         const double sig64 = mx > 0.0 ? mx / (double)Q::qmax : 1.0;
         for (int n = lane; n < n_cols; n += 32) {
-            double2 d = weight_at64(f, tau, mask, b, n, N, B);
+            double2 d = weight_at64(ph, mask, b, n, N, B);
             const double re = d.x / sig64, im = d.y / sig64;
             put(n, Q::q(re), Q::q(im), Q::q(-im));
         }
@@ -259,21 +307,23 @@ static int fmt_code(const bf_plan *p)
 cudaError_t launch_delays(bf_plan *p, cudaStream_t s)
 {
     int total = p->N * p->B;
-    k_delays<<<(total + 255) / 256, 256, 0, s>>>(p->d_pos, p->d_dirs, p->N, p->B, p->d_tau);
+    k_delays<<<(total + 255) / 256, 256, 0, s>>>(p->d_pos, p->d_dirs, p->N, p->B, p->f0, p->df, p->d_tau,
+                                                 p->d_ab);
     return cudaGetLastError();
 }
 
-cudaError_t launch_weights(bf_plan *p, cudaStream_t s)
+template <bool FIXED>
+static void weights_launch(bf_plan *p, cudaStream_t s)
 {
     dim3 grid((p->wf.b_pad + 7) / 8, p->C);
     const WeightFormat &f = p->wf;
-#define BF_W_LAUNCH(F)                                                                                 \
-    k_weights_tc<F><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_mask, p->N, p->B, f.b_pad, f.k_pad, \
-                                         p->d_w, p->d_wscale, p->d_wsig)
+#define BF_W_LAUNCH(F)                                                                                      \
+    k_weights_tc<F, FIXED><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_ab, p->d_mask, p->N, p->B, f.b_pad, \
+                                                f.k_pad, p->d_w, p->d_wscale, p->d_wsig)
     switch (fmt_code(p)) {
     case kFmtSimt:
-        k_weights_simt<0><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_mask, p->N, p->B, f.b_pad,
-                                               (float2 *)p->d_w, p->d_wscale, p->d_wsig);
+        k_weights_simt<FIXED><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_ab, p->d_mask, p->N, p->B,
+                                                   f.b_pad, (float2 *)p->d_w, p->d_wscale, p->d_wsig);
         break;
     case kFmtF16: BF_W_LAUNCH(kFmtF16); break;
     case kFmtBF16: BF_W_LAUNCH(kFmtBF16); break;
@@ -281,6 +331,12 @@ cudaError_t launch_weights(bf_plan *p, cudaStream_t s)
     default: BF_W_LAUNCH(kFmtI8); break;
     }
 #undef BF_W_LAUNCH
+}
+
+cudaError_t launch_weights(bf_plan *p, cudaStream_t s)
+{
+    if (p->uniform_freqs) weights_launch<true>(p, s);
+    else weights_launch<false>(p, s);
     return cudaGetLastError();
 }
 

@@ -93,9 +93,28 @@ def test_weights_fp32_match_fp64(bf):
     plan.close()
 
 
+def test_weights_fp32_nonuniform_channels(bf):
+    """Channel lists that are not uniformly spaced take the per-weight FP64
+    phase reduction instead of the fixed-point recurrence."""
+    scene, dirs, _ = synth.config1()
+    freqs = np.sort(np.random.default_rng(4).uniform(300e6, 800e6, size=16))
+    plan = bf.Plan(scene.pos, freqs, dirs, bf.BF_C32, 16)
+    w, _ = plan.export_weights()
+    plan.sync()
+    W = w.cpu().numpy().astype(np.float64)
+    W = W[..., 0] + 1j * W[..., 1]
+    err = np.max(np.abs(W - oracle.weights(scene.pos, freqs, dirs)))
+    record("weights_fp32_nonuniform", float(err), 0.0, mode="c32")
+    assert err < 5e-7
+    plan.close()
+
+
+@pytest.mark.parametrize("uniform", [True, False])
 @pytest.mark.parametrize("mode", [synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8])
-def test_weights_quantised_are_the_rounding_of_the_exact_weights(bf, mode):
+def test_weights_quantised_are_the_rounding_of_the_exact_weights(bf, mode, uniform):
     scene = small_scene(n_ant=64, n_chan=8, grid=False, extent=200.0)
+    if not uniform:
+        scene.freqs = np.sort(np.random.default_rng(6).uniform(350e6, 450e6, size=8))
     dirs = synth.beam_grid(16, 12)
     mask = np.ones(64, np.uint8)
     mask[[5, 40]] = 0
