@@ -21,7 +21,7 @@
 //                NT-column FP32 accumulators (the epilogue drains one while
 //                the next tile accumulates)
 //   warps 2-17   epilogue, four warps per TMEM lane quarter, each on a slice
-//                of the tile's columns: one 64-column tcgen05.ld per wait,
+//                of the tile's columns: one 32-column tcgen05.ld per wait,
 //                squares, window sums in a fixed order, re+im combination via
 //                one shuffle (the two rows of a beam are 16 lanes apart); the
 //                window powers of a tile are staged in shared memory and one
@@ -98,7 +98,7 @@ __device__ __forceinline__ float sumsq16(const float *v)
 }
 
 template <bool F8, bool FASTWIN, bool COMPLEX>
-__global__ void __maxnreg__(112)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -348,12 +348,12 @@ __global__ void __maxnreg__(112)
                                 ++wi;
                             };
                             int col = 0;
-                            for (; col + 64 <= cols; col += 64) {
-                                float v[64];
-                                tmem_ld64(taddr + col, v);
+                            for (; col + 32 <= cols; col += 32) {
+                                float v[32];
+                                tmem_ld32(taddr + col, v);
                                 if (FASTWIN) {
 #pragma unroll
-                                    for (int k = 0; k < 4; ++k) {
+                                    for (int k = 0; k < 2; ++k) {
                                         ws += sumsq16(v + 16 * k);
                                         cnt += 16;
                                         if (cnt == a.t_int) {
@@ -364,7 +364,7 @@ __global__ void __maxnreg__(112)
                                     }
                                 } else {
 #pragma unroll
-                                    for (int i = 0; i < 64; ++i) {
+                                    for (int i = 0; i < 32; ++i) {
                                         ws = fmaf(v[i], v[i], ws);
                                         if (++cnt == a.t_int) {
                                             emit(ws);
