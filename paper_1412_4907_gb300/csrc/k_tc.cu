@@ -48,7 +48,7 @@ constexpr int kEpiWarps = 16;
 constexpr int kTcThreads = (2 + kEpiWarps) * 32;
 constexpr int kTmemCols = 512;
 constexpr int kMaxWinPerTile = 16;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
 
 struct TcKernelArgs {
     long long ct_total;                 // channels x time tiles
@@ -78,9 +78,9 @@ __device__ __forceinline__ void group_tiles(const TcKernelArgs &a, int g, int &m
 // Bounded wait that ignores the abort flag (used only to drain on abort).
 __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity)
 {
-    const uint64_t t0 = global_ns();
+    const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 200000000ull) break;   // 0.2 s
+        if (clock64() - t0 > 400000000ll) break;   // ~0.2 s
 }
 
 // Sum of squares of 16 values with four independent chains.
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 group_tiles(a, g, m0, gs);
                 int c = c_first, tt = tt_first;
                 for (long long ct = ct0; ct < ct1; ++ct) {
-                    if (!mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitNs)) {
+                    if (!mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
                     }
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (ct == ct0 || tt == 0) {   // weights of (group, channel)
                         for (int s = 0; s < gs; ++s) {
                             if (!mbar_wait(b_wempty + 8 * s, ((wcnt >> s) & 1u) ^ 1u, abort_flag, a.err,
-                                           kWaitLimitNs)) {
+                                           kWaitLimitCycles)) {
                                 ok = false;
                                 break;
                             }
@@ -225,21 +225,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (long long ct = ct0; ct < ct1 && ok; ++ct) {
                     const bool neww = (ct == ct0) || tt == 0;
                     const bool lastw = (ct + 1 == ct1) || tt + 1 == a.t_tiles;
-                    if (!mbar_wait(b_xfull + 8 * xs, (xpar >> xs) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                    if (!mbar_wait(b_xfull + 8 * xs, (xpar >> xs) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
                     }
                     xpar ^= 1u << xs;
                     for (int s = 0; s < gs; ++s) {
                         if (neww) {
-                            if (!mbar_wait(b_wfull + 8 * s, (wpar >> s) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                            if (!mbar_wait(b_wfull + 8 * s, (wpar >> s) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                                 ok = false;
                                 break;
                             }
                             wpar ^= 1u << s;
                         }
                         if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err,
-                                       kWaitLimitNs)) {
+                                       kWaitLimitCycles)) {
                             ok = false;
                             break;
                         }
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (long long ct = ct0; ct < ct1 && ok; ++ct) {
                 const int cg = a.c_base + c;
                 for (int s = 0; s < gs; ++s) {
-                    if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                    if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
                     }
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (!COMPLEX && active) {
                         // the staging buffer of this accumulator is free once the previous
                         // tile that used it has been written out
-                        if (!mbar_wait(sempty, ((epar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitNs)) {
+                        if (!mbar_wait(sempty, ((epar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                             ok = false;
                             break;
                         }
@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
                     } else {
                         if (active) {
-                            const float scale = bvalid ? a.wscale[(size_t)cg * a.b_pad + b] : 0.f;
+                            const float scale =
+                                bvalid ? (a.wscale ? a.wscale[(size_t)cg * a.b_pad + b] : 1.f) : 0.f;
                             float ws = 0.f;
                             int wi = 0, cnt = 0;
                             auto emit = [&](float sum) {
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         if (active && h == 0) {
                             // the slices of this quarter are staged: one warp writes each
                             // beam's run of windows with vector stores
-                            if (!mbar_wait(sfull, (spar >> acc) & 1u, abort_flag, a.err, kWaitLimitNs)) {
+                            if (!mbar_wait(sfull, (spar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                                 ok = false;
                                 break;
                             }
@@ -606,7 +607,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
                ((uint32_t)(kRowsPerMTile >> 4) << 24);
     ka.x_stage_bytes = (uint32_t)(f.kb * cfg.nt * 128);
     ka.w_slot_bytes = (uint32_t)(f.kb * 16384);
-    ka.wscale = p->d_wscale;
+    ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
     ka.err = p->d_err;

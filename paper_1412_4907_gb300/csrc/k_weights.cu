@@ -25,6 +25,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "bf_internal.h"
 
 namespace bfi {
@@ -208,11 +210,11 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
     const size_t m_pad = (size_t)(b_pad / kBeamsPerMTile) * kRowsPerMTile;
     T *p_re = reinterpret_cast<T *>(w) + ((size_t)c * m_pad + row_re) * k_pad;
     T *p_im = p_re + (size_t)16 * k_pad;   // the im row sits 16 rows below
+    // re row: (Re W, -Im W); im row: (Im W, Re W) -- one store per row pair
+    using T2 = typename std::conditional<sizeof(T) == 2, uint32_t, uint16_t>::type;
     auto put = [&](int n, T qre, T qim, T qim_neg) {
-        p_re[2 * n] = qre;       // re row: ( Re W, -Im W)
-        p_re[2 * n + 1] = qim_neg;
-        p_im[2 * n] = qim;       // im row: ( Im W,  Re W)
-        p_im[2 * n + 1] = qre;
+        reinterpret_cast<T2 *>(p_re)[n] = (T2)qre | ((T2)qim_neg << (8 * sizeof(T)));
+        reinterpret_cast<T2 *>(p_im)[n] = (T2)qim | ((T2)qre << (8 * sizeof(T)));
     };
     bool redo = false;
     for (int n = lane; n < n_cols; n += 32) {
@@ -221,7 +223,11 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
             put(n, T(0), T(0), T(0));
             continue;
         }
-        float re = v.x / sig, im = v.y / sig;
+        float re = v.x, im = v.y;
+        if (scaled) {
+            re /= sig;
+            im /= sig;
+        }
         const float dre = delta + 4e-7f * fabsf(re), dim = delta + 4e-7f * fabsf(im);
         const bool near = !same_value<Q>(Q::q(re - dre), Q::q(re + dre)) ||
                           !same_value<Q>(Q::q(im - dim), Q::q(im + dim));

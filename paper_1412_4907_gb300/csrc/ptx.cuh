@@ -57,21 +57,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 enum : unsigned { kErrTimeout = 1u };
 
 // Wait for the phase with `parity` of barrier `bar` to complete, for at most
-// `limit_ns` nanoseconds.  On timeout, record it in *err, raise the CTA-wide
-// abort flag and return false.  Also returns false as soon as another role
-// of the CTA has raised the abort flag.
+// `limit_cycles` SM clock cycles (about 1 s per 2e9 at the maximum clock).
+// On timeout, record it in *err, raise the CTA-wide abort flag and return
+// false.  Also returns false once another role of the CTA has raised the
+// abort flag.  The abort flag and the cycle counter are read only every 64
+// polls: try_wait itself suspends the thread for a while when the phase is
+// not complete, so a poll is cheap but not free.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned *err, uint64_t limit_ns)
+                                          unsigned *err, uint64_t limit_cycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
+    const long long t0 = clock64();
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (global_ns() - t0 > limit_ns) {
-            *abort_flag = 1;
-            atomicOr(err, kErrTimeout);
-            return false;
+        if ((i & 63u) == 0) {
+            if (*abort_flag) return false;
+            if ((uint64_t)(clock64() - t0) > limit_cycles) {
+                *abort_flag = 1;
+                atomicOr(err, kErrTimeout);
+                return false;
+            }
         }
     }
 }
