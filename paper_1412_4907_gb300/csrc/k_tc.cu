@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         }
                         tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(b_tempty + 8 * acc);
+                        if (lane == 0) mbar_arrive_relaxed(b_tempty + 8 * acc);
                     } else {
                         if (active) {
                             const float scale =
@@ -402,8 +402,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) {
-                            mbar_arrive(b_tempty + 8 * acc);
-                            if (active) mbar_arrive(sfull);
+                            mbar_arrive_relaxed(b_tempty + 8 * acc);
+                            // slices 1..3 publish their staged windows to slice 0
+                            if (active) {
+                                if (h == 0) mbar_arrive_relaxed(sfull);
+                                else mbar_arrive(sfull);
+                            }
                         }
                         if (active && h == 0) {
                             // the slices of this quarter are staged: one warp writes each
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 }
                             }
                             __syncwarp();
-                            if (lane == 0) mbar_arrive(sempty);
+                            if (lane == 0) mbar_arrive_relaxed(sempty);
                         }
                     }
                     acc ^= 1;

@@ -217,7 +217,8 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
         reinterpret_cast<T2 *>(p_im)[n] = (T2)qim | ((T2)qre << (8 * sizeof(T)));
     };
     bool redo = false;
-    for (int n = lane; n < n_cols; n += 32) {
+    uint32_t near_bits = 0;   // antennas lane + 32k of this lane near a boundary (k < 32)
+    for (int n = lane, k = 0; n < n_cols; n += 32, ++k) {
         float2 v = weight_at(ph, mask, b, n, N, B);
         if (v.x == 0.f && v.y == 0.f) {   // masked antenna, padding beam or padding column
             put(n, T(0), T(0), T(0));
@@ -231,13 +232,18 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
         const float dre = delta + 4e-7f * fabsf(re), dim = delta + 4e-7f * fabsf(im);
         const bool near = !same_value<Q>(Q::q(re - dre), Q::q(re + dre)) ||
                           !same_value<Q>(Q::q(im - dim), Q::q(im + dim));
-        if (near && !scaled) {
-            double2 d = weight_at64(ph, mask, b, n, N, B);
-            put(n, Q::q(d.x), Q::q(d.y), Q::q(-d.y));
-        } else {
-            put(n, Q::q(re), Q::q(im), Q::q(-im));
-        }
+        put(n, Q::q(re), Q::q(im), Q::q(-im));
+        if (near) near_bits |= 1u << (k & 31);
         redo |= near;
+    }
+    // FP64 recomputation of the few components near a boundary, in a separate
+    // warp-uniform pass so the FP64 code is branched around, not predicated
+    if (!scaled && __any_sync(0xffffffffu, near_bits != 0)) {
+        for (int n = lane, k = 0; n < n_cols; n += 32, ++k)
+            if (near_bits & (1u << (k & 31))) {
+                double2 d = weight_at64(ph, mask, b, n, N, B);
+                put(n, Q::q(d.x), Q::q(d.y), Q::q(-d.y));
+            }
     }
     if (scaled && __any_sync(0xffffffffu, redo)) {
         double mx = 0.0;
