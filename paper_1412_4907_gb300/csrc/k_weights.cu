@@ -65,7 +65,14 @@ struct Phase {
         if (FIXED) {
             const size_t i = (size_t)b * N + n;
             const unsigned long long ph = ab[2 * i] + c * ab[2 * i + 1];   // modulo 2^64
-            return (float)(int)(ph >> 32) * 4.656612873077393e-10f;        // x 2^-31
+            // top 32 bits as a signed value times 2^-31, without an integer
+            // conversion instruction: the two 16-bit halves become floats
+            // exactly through the 1.5 * 2^23 bias, and one FMA rounds once
+            const int hi = (int)(ph >> 32);
+            const float m = 12582912.0f;
+            const float h16 = __int_as_float(0x4B400000 + (hi >> 16)) - m;        // exact, signed
+            const float l16 = __int_as_float(0x4B400000 + (hi & 0xFFFF)) - m;     // exact, 0..65535
+            return __fmaf_rn(h16, 3.0517578125e-05f, l16 * 4.656612873077393e-10f);  // 2^-15, 2^-31
         }
         double ph = f * tau[(size_t)b * N + n];   // cycles
         double r = ph - rint(ph);                 // [-1/2, 1/2]
@@ -115,38 +122,64 @@ struct Quant<kFmtF16> {
     using T = uint16_t;
     static constexpr float qmax = 0.f;
     static constexpr T mag = 0x7FFF;
-    __device__ static T q(float x) { return __half_as_ushort(__float2half_rn(x)); }
     __device__ static T q(double x) { return __half_as_ushort(__double2half(x)); }
+    __device__ static uint32_t q2(float a, float b)
+    {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
 };
 template <>
 struct Quant<kFmtBF16> {
     using T = uint16_t;
     static constexpr float qmax = 0.f;
     static constexpr T mag = 0x7FFF;
-    __device__ static T q(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
     __device__ static T q(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
+    __device__ static uint32_t q2(float a, float b)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
 };
 template <>
 struct Quant<kFmtE4M3> {
     using T = uint8_t;
     static constexpr float qmax = 448.f;
     static constexpr T mag = 0x7F;
-    __device__ static T q(float x) { return (T)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
     __device__ static T q(double x) { return (T)__nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
+    __device__ static uint16_t q2(float a, float b)
+    {
+        return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    }
 };
 template <>
 struct Quant<kFmtI8> {
     using T = uint16_t;   // stored as FP16 integers
     static constexpr float qmax = 127.f;
     static constexpr T mag = 0x7FFF;
-    __device__ static T q(float x) { return __half_as_ushort(__float2half_rn(fminf(fmaxf(rintf(x), -127.f), 127.f))); }
     __device__ static T q(double x) { return __half_as_ushort(__double2half(fmin(fmax(rint(x), -127.0), 127.0))); }
+    // round to the nearest integer, ties to even, with two FP32 adds
+    // (exact for |x| < 2^22), clip, then pack to FP16 (exact for integers)
+    __device__ static float rnd(float x)
+    {
+        const float m = 12582912.0f;   // 1.5 * 2^23
+        return fminf(fmaxf(__fsub_rn(__fadd_rn(x, m), m), -127.f), 127.f);
+    }
+    __device__ static uint32_t q2(float a, float b)
+    {
+        __half2 h = __floats2half2_rn(rnd(a), rnd(b));
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
 };
 
-// Two stored codes of the same value (+0 and -0 count as equal).
+// Do the two codes packed in `pair` (low, high) store the same value?
+// (+0 and -0 count as equal)
 template <class Q>
-__device__ __forceinline__ bool same_value(typename Q::T a, typename Q::T b)
+__device__ __forceinline__ bool pair_same(uint32_t pair)
 {
+    constexpr int bits = 8 * sizeof(typename Q::T);
+    constexpr uint32_t one = (1u << bits) - 1u;
+    const uint32_t a = pair & one, b = (pair >> bits) & one;
     return a == b || ((a & Q::mag) == 0 && (b & Q::mag) == 0);
 }
 
@@ -210,7 +243,8 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
     const size_t m_pad = (size_t)(b_pad / kBeamsPerMTile) * kRowsPerMTile;
     T *p_re = reinterpret_cast<T *>(w) + ((size_t)c * m_pad + row_re) * k_pad;
     T *p_im = p_re + (size_t)16 * k_pad;   // the im row sits 16 rows below
-    // re row: (Re W, -Im W); im row: (Im W, Re W) -- one store per row pair
+    // re row: (Re W, -Im W); im row: (Im W, Re W) -- one packed conversion and
+    // one store per row pair (packed conversions run on the FP32 pipes)
     using T2 = typename std::conditional<sizeof(T) == 2, uint32_t, uint16_t>::type;
     auto put = [&](int n, T qre, T qim, T qim_neg) {
         reinterpret_cast<T2 *>(p_re)[n] = (T2)qre | ((T2)qim_neg << (8 * sizeof(T)));
@@ -230,9 +264,9 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
             im /= sig;
         }
         const float dre = delta + 4e-7f * fabsf(re), dim = delta + 4e-7f * fabsf(im);
-        const bool near = !same_value<Q>(Q::q(re - dre), Q::q(re + dre)) ||
-                          !same_value<Q>(Q::q(im - dim), Q::q(im + dim));
-        put(n, Q::q(re), Q::q(im), Q::q(-im));
+        const bool near = !pair_same<Q>(Q::q2(re - dre, re + dre)) || !pair_same<Q>(Q::q2(im - dim, im + dim));
+        reinterpret_cast<T2 *>(p_re)[n] = (T2)Q::q2(re, -im);
+        reinterpret_cast<T2 *>(p_im)[n] = (T2)Q::q2(im, re);
         if (near) near_bits |= 1u << (k & 31);
         redo |= near;
     }
