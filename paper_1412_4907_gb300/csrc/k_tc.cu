@@ -21,11 +21,13 @@
 //                NT-column FP32 accumulators (the epilogue drains one while
 //                the next tile accumulates)
 //   warps 2-17   epilogue, four warps per TMEM lane quarter, each on a slice
-//                of the tile's columns: one 32-column tcgen05.ld per wait,
-//                squares, window sums in a fixed order, re+im combination via
-//                one shuffle (the two rows of a beam are 16 lanes apart); the
-//                window powers of a tile are staged in shared memory and one
-//                warp per quarter writes each beam's run as 16-byte stores.
+//                of the tile's columns: the slice is read with 64-column
+//                tcgen05.ld and the accumulator handed back to the MMA before
+//                any arithmetic; then squares, window sums in a fixed order,
+//                re+im combination via one shuffle (the two rows of a beam
+//                are 16 lanes apart), window powers staged in shared memory
+//   warp 18      store warp: writes each staged tile as one run of windows
+//                per beam (16-byte stores), four tiles in flight.
 // Work: the M tiles of a channel are split into weight groups; the CTAs are
 // arranged as P sets of Gq CTAs, the CTAs of one set hold different groups
 // and walk the same (channel, time-tile) range in step, so a voltage tile is
@@ -45,7 +47,9 @@
 namespace bfi {
 
 constexpr int kEpiWarps = 16;
-constexpr int kTcThreads = (2 + kEpiWarps) * 32;
+constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
+constexpr int kTcThreads = (3 + kEpiWarps) * 32;
+constexpr int kStageDepth = 4;                     // staged tiles in flight
 constexpr int kTmemCols = 512;
 constexpr int kMaxWinPerTile = 16;
 constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t sx = base;
     const uint32_t sw = sx + 2 * a.x_stage_bytes;
     float *stage = reinterpret_cast<float *>(gbase + 2 * a.x_stage_bytes + a.gmax * a.w_slot_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * kBeamsPerMTile * kMaxWinPerTile);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
     const uint32_t b_xfull = smem_u32(bars + 0);
     const uint32_t b_xempty = smem_u32(bars + 2);
     const uint32_t b_tfull = smem_u32(bars + 4);
@@ -116,9 +120,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t b_drain = smem_u32(bars + 8);
     const uint32_t b_wfull = smem_u32(bars + 9);
     const uint32_t b_wempty = smem_u32(bars + 9 + a.gmax);
-    const uint32_t b_sfull = smem_u32(bars + 9 + 2 * a.gmax);   // [acc][quarter]: slices staged
-    const uint32_t b_sempty = b_sfull + 8 * 8;                   // [acc][quarter]: staging read out
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 9 + 2 * a.gmax + 16);
+    const uint32_t b_sfull = smem_u32(bars + 9 + 2 * a.gmax);   // [stage]: every slice staged
+    const uint32_t b_sempty = b_sfull + 8 * kStageDepth;         // [stage]: written out
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 9 + 2 * a.gmax + 2 * kStageDepth);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -136,9 +140,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(b_wfull + 8 * s, 1);
             mbar_init(b_wempty + 8 * s, 1);
         }
-        for (int i = 0; i < 8; ++i) {
-            mbar_init(b_sfull + 8 * i, a.nsplit);
-            mbar_init(b_sempty + 8 * i, 1);
+        for (int i = 0; i < kStageDepth; ++i) {
+            mbar_init(b_sfull + 8 * i, 4 * a.nsplit);   // the active epilogue warps
+            mbar_init(b_sempty + 8 * i, 1);             // the store warp
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             drain_wait(b_drain, 0);
         }
         __syncwarp();
-    } else {
+    } else if (warp < kStoreWarp) {
         // -------------------------------------------------------------- epilogue
         const int e = warp - 2;
         const int q = warp & 3;               // TMEM lane quarter this warp may access
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int col0 = h * cols;
         const bool active = h < a.nsplit;
         const int wps = COMPLEX ? 0 : cols / a.t_int;   // windows per slice
-        uint32_t tpar = 0, spar = 0, epar = 0;
+        uint32_t tpar = 0, kt = 0;
         int acc = 0;
         bool ok = true;
         for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
@@ -288,28 +292,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int c = c_first, tt = tt_first;
             for (long long ct = ct0; ct < ct1 && ok; ++ct) {
                 const int cg = a.c_base + c;
-                for (int s = 0; s < gs; ++s) {
+                for (int s = 0; s < gs; ++s, ++kt) {
                     if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
                     }
                     tpar ^= 1u << acc;
-                    const uint32_t sfull = b_sfull + 8 * (acc * 4 + q), sempty = b_sempty + 8 * (acc * 4 + q);
+                    const uint32_t sb = kt % kStageDepth;
+                    const uint32_t use = kt / kStageDepth;
                     if (!COMPLEX && active) {
-                        // the staging buffer of this accumulator is free once the previous
-                        // tile that used it has been written out
-                        if (!mbar_wait(sempty, ((epar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                        // this staging buffer is free once the store warp has written out
+                        // the tile that used it kStageDepth tiles ago
+                        if (!mbar_wait(b_sempty + 8 * sb, (use & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                             ok = false;
                             break;
                         }
-                        epar ^= 1u << acc;
                     }
                     tc_fence_after();
-                    const int b_tile0 = (m0 + s) * kBeamsPerMTile;
-                    const int b = b_tile0 + bq;
+                    const int b = (m0 + s) * kBeamsPerMTile + bq;
                     const bool bvalid = b < a.B;
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
-                    float *stg = stage + acc * (kBeamsPerMTile * kMaxWinPerTile);
+                    // hand the accumulator back to the MMA as soon as it has been read
+                    auto release = [&]() {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_relaxed(b_tempty + 8 * acc);
+                    };
                     if (COMPLEX) {
                         if (active) {
                             const float sg = bvalid ? a.wsig[(size_t)cg * a.b_pad + b] : 0.f;
@@ -334,119 +342,107 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 }
                             }
                         }
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive_relaxed(b_tempty + 8 * acc);
+                        release();
+                    } else if (!active) {
+                        release();
                     } else {
-                        if (active) {
-                            const float scale =
-                                bvalid ? (a.wscale ? a.wscale[(size_t)cg * a.b_pad + b] : 1.f) : 0.f;
-                            float ws = 0.f;
-                            int wi = 0, cnt = 0;
-                            auto emit = [&](float sum) {
-                                const float pw = (sum + __shfl_xor_sync(0xffffffffu, sum, 16)) * scale;
-                                if (part == 0) stg[bq * kMaxWinPerTile + h * wps + wi] = pw;
-                                ++wi;
-                            };
-                            int col = 0;
-                            for (; col + 32 <= cols; col += 32) {
-                                float v[32];
-                                tmem_ld32(taddr + col, v);
-                                if (FASTWIN) {
-#pragma unroll
-                                    for (int k = 0; k < 2; ++k) {
-                                        ws += sumsq16(v + 16 * k);
-                                        cnt += 16;
-                                        if (cnt == a.t_int) {
-                                            emit(ws);
-                                            ws = 0.f;
-                                            cnt = 0;
-                                        }
-                                    }
-                                } else {
-#pragma unroll
-                                    for (int i = 0; i < 32; ++i) {
-                                        ws = fmaf(v[i], v[i], ws);
-                                        if (++cnt == a.t_int) {
-                                            emit(ws);
-                                            ws = 0.f;
-                                            cnt = 0;
-                                        }
-                                    }
+                        const float scale = bvalid ? (a.wscale ? a.wscale[(size_t)cg * a.b_pad + b] : 1.f) : 0.f;
+                        float *stg = stage + sb * (kBeamsPerMTile * kMaxWinPerTile);
+                        float ws = 0.f;
+                        int wi = 0, cnt = 0;
+                        auto emit = [&](float sum) {
+                            const float pw = (sum + __shfl_xor_sync(0xffffffffu, sum, 16)) * scale;
+                            if (part == 0) stg[bq * kMaxWinPerTile + h * wps + wi] = pw;
+                            ++wi;
+                        };
+                        auto add16 = [&](const float *v) {
+                            if (FASTWIN) {
+                                ws += sumsq16(v);
+                                cnt += 16;
+                                if (cnt == a.t_int) {
+                                    emit(ws);
+                                    ws = 0.f;
+                                    cnt = 0;
                                 }
-                            }
-                            for (; col < cols; col += 16) {
-                                float v[16];
-                                tmem_ld16(taddr + col, v);
-                                if (FASTWIN) {
-                                    ws += sumsq16(v);
-                                    cnt += 16;
-                                    if (cnt == a.t_int) {
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) {
+                                    ws = fmaf(v[i], v[i], ws);
+                                    if (++cnt == a.t_int) {
                                         emit(ws);
                                         ws = 0.f;
                                         cnt = 0;
                                     }
-                                } else {
+                                }
+                            }
+                        };
+                        const int n64 = cols / 64, rem = cols % 64;   // rem is a multiple of 16
+                        for (int bt = 0; bt < n64; ++bt) {
+                            float v[64];
+                            tmem_ld64(taddr + bt * 64, v);
+                            if (bt == n64 - 1 && rem == 0) release();
 #pragma unroll
-                                    for (int i = 0; i < 16; ++i) {
-                                        ws = fmaf(v[i], v[i], ws);
-                                        if (++cnt == a.t_int) {
-                                            emit(ws);
-                                            ws = 0.f;
-                                            cnt = 0;
-                                        }
-                                    }
-                                }
-                            }
+                            for (int k = 0; k < 4; ++k) add16(v + 16 * k);
                         }
-                        tc_fence_before();
+                        for (int col = n64 * 64; col < cols; col += 16) {
+                            float v[16];
+                            tmem_ld16(taddr + col, v);
+                            if (col + 16 == cols) release();
+                            add16(v);
+                        }
                         __syncwarp();
-                        if (lane == 0) {
-                            mbar_arrive_relaxed(b_tempty + 8 * acc);
-                            // slices 1..3 publish their staged windows to slice 0
-                            if (active) {
-                                if (h == 0) mbar_arrive_relaxed(sfull);
-                                else mbar_arrive(sfull);
-                            }
-                        }
-                        if (active && h == 0) {
-                            // the slices of this quarter are staged: one warp writes each
-                            // beam's run of windows with vector stores
-                            if (!mbar_wait(sfull, (spar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
-                                ok = false;
-                                break;
-                            }
-                            spar ^= 1u << acc;
-                            {
-                                const int j0 = tt * a.wpt;
-                                const int nj = min(a.wpt, a.T_o - j0);
-                                if ((a.T_o & 3) == 0 && (a.wpt & 3) == 0) {
-                                    const int per = a.wpt >> 2;
-                                    for (int i = lane; i < 16 * per; i += 32) {
-                                        const int bl = i / per, k = (i % per) * 4;
-                                        const int bb = b_tile0 + q * 16 + bl;
-                                        if (bb < a.B && k < nj) {
-                                            const float4 v4 = *reinterpret_cast<const float4 *>(
-                                                stg + (q * 16 + bl) * kMaxWinPerTile + k);
-                                            *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o +
-                                                                        j0 + k) = v4;
-                                        }
-                                    }
-                                } else {
-                                    for (int i = lane; i < 16 * a.wpt; i += 32) {
-                                        const int bl = i / a.wpt, k = i % a.wpt;
-                                        const int bb = b_tile0 + q * 16 + bl;
-                                        if (bb < a.B && k < nj)
-                                            a.out[((size_t)bb * a.c_total + cg) * a.T_o + j0 + k] =
-                                                stg[(q * 16 + bl) * kMaxWinPerTile + k];
-                                    }
-                                }
-                            }
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive_relaxed(sempty);
-                        }
+                        if (lane == 0) mbar_arrive(b_sfull + 8 * sb);   // publishes the staged windows
                     }
                     acc ^= 1;
+                }
+                if (++tt == a.t_tiles) {
+                    tt = 0;
+                    ++c;
+                }
+            }
+        }
+    } else if (warp == kStoreWarp && !COMPLEX) {
+        // ------------------------------------------------------------ store warp
+        // writes each staged tile as one run of windows per beam
+        uint32_t kt = 0;
+        bool ok = true;
+        const bool vec = (a.T_o & 3) == 0 && (a.wpt & 3) == 0;
+        for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+            int m0, gs;
+            group_tiles(a, g, m0, gs);
+            int c = c_first, tt = tt_first;
+            for (long long ct = ct0; ct < ct1 && ok; ++ct) {
+                const int cg = a.c_base + c;
+                const int j0 = tt * a.wpt;
+                const int nj = min(a.wpt, a.T_o - j0);
+                for (int s = 0; s < gs; ++s, ++kt) {
+                    const uint32_t sb = kt % kStageDepth;
+                    if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                        ok = false;
+                        break;
+                    }
+                    const float *stg = stage + sb * (kBeamsPerMTile * kMaxWinPerTile);
+                    const int b_tile0 = (m0 + s) * kBeamsPerMTile;
+                    if (vec) {
+                        const int per = a.wpt >> 2;
+                        for (int i = lane; i < kBeamsPerMTile * per; i += 32) {
+                            const int bl = i / per, k = (i % per) * 4;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && k < nj) {
+                                const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile + k);
+                                *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o + j0 + k) = v4;
+                            }
+                        }
+                    } else {
+                        for (int i = lane; i < kBeamsPerMTile * a.wpt; i += 32) {
+                            const int bl = i / a.wpt, k = i % a.wpt;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && k < nj)
+                                a.out[((size_t)bb * a.c_total + cg) * a.T_o + j0 + k] = stg[bl * kMaxWinPerTile + k];
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
                 }
                 if (++tt == a.t_tiles) {
                     tt = 0;
@@ -490,8 +486,8 @@ static int gcd_i(int x, int y)
     return x;
 }
 
-static int ctrl_bytes() { return 8 * (9 + 2 * 16 + 16) + 16; }
-static int stage_bytes() { return 2 * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
+static int ctrl_bytes() { return 8 * (9 + 2 * 16 + 2 * kStageDepth) + 16; }
+static int stage_bytes() { return kStageDepth * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
 
 bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
 {
