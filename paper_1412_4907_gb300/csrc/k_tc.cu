@@ -101,7 +101,27 @@ __device__ __forceinline__ float sumsq16(const float *v)
     return (s0 + s1) + (s2 + s3);
 }
 
-template <bool F8, bool FASTWIN, bool COMPLEX>
+__device__ __forceinline__ float sumsq32(const float *v)
+{
+    return sumsq16(v) + sumsq16(v + 16);
+}
+
+// Sum of squares of 64 values with eight independent chains.
+__device__ __forceinline__ float sumsq64(const float *v)
+{
+    float s[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 64; i += 8)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = fmaf(v[i + j], v[i + j], s[j]);
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+// WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
+// -1 = any T_int (per-column window counter).
+template <bool F8, int WIN, bool COMPLEX>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
 {
@@ -356,7 +376,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             ++wi;
                         };
                         auto add16 = [&](const float *v) {
-                            if (FASTWIN) {
+                            if (WIN >= 0) {
                                 ws += sumsq16(v);
                                 cnt += 16;
                                 if (cnt == a.t_int) {
@@ -381,8 +401,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             float v[64];
                             tmem_ld64(taddr + bt * 64, v);
                             if (bt == n64 - 1 && rem == 0) release();
+                            if (WIN == 64) {
+                                emit(sumsq64(v));
+                            } else if (WIN == 32) {
+                                emit(sumsq32(v));
+                                emit(sumsq32(v + 32));
+                            } else if (WIN == 16) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) add16(v + 16 * k);
+                                for (int k = 0; k < 4; ++k) emit(sumsq16(v + 16 * k));
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) add16(v + 16 * k);
+                            }
                         }
                         for (int col = n64 * 64; col < cols; col += 16) {
                             float v[16];
@@ -423,7 +453,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     const float *stg = stage + sb * (kBeamsPerMTile * kMaxWinPerTile);
                     const int b_tile0 = (m0 + s) * kBeamsPerMTile;
-                    if (vec) {
+                    if (vec && a.wpt == 4) {
+                        // one float4 per beam: lanes take beams lane and lane + 32
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int bl = lane + 32 * r;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && nj > 0) {
+                                const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile);
+                                *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o + j0) = v4;
+                            }
+                        }
+                    } else if (vec) {
                         const int per = a.wpt >> 2;
                         for (int i = lane; i < kBeamsPerMTile * per; i += 32) {
                             const int bl = i / per, k = (i % per) * 4;
@@ -533,11 +574,11 @@ bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
     return false;
 }
 
-template <bool F8, bool FW, bool CPX>
+template <bool F8, int WIN, bool CPX>
 static cudaError_t launch_one(const CUtensorMap &xm, const CUtensorMap &wm, const TcKernelArgs &ka, int grid,
                               int smem, cudaStream_t s)
 {
-    auto kern = k_tc<F8, FW, CPX>;
+    auto kern = k_tc<F8, WIN, CPX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kTcThreads, smem, s>>>(xm, wm, ka);
@@ -617,17 +658,24 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const long long n_sets = std::max<long long>(1, std::min<long long>(p->num_sms / ka.gq, ka.ct_total));
     const int grid = (int)(n_sets * ka.gq);
     const bool f8 = f.op == kOpE4M3;
-    const bool fw = cfg.fast_windows;
     if (ta.complex_out) {
-        if (f8) return launch_one<true, true, true>(xm, wm, ka, grid, cfg.smem, s);
-        return launch_one<false, true, true>(xm, wm, ka, grid, cfg.smem, s);
+        if (f8) return launch_one<true, 0, true>(xm, wm, ka, grid, cfg.smem, s);
+        return launch_one<false, 0, true>(xm, wm, ka, grid, cfg.smem, s);
+    }
+    const int win = (ta.t_int == 64 || ta.t_int == 32 || ta.t_int == 16) ? ta.t_int : (ta.t_int % 16 == 0 ? 0 : -1);
+#define BF_TC_WIN(F8V)                                                         \
+    switch (win) {                                                             \
+    case 64: return launch_one<F8V, 64, false>(xm, wm, ka, grid, cfg.smem, s); \
+    case 32: return launch_one<F8V, 32, false>(xm, wm, ka, grid, cfg.smem, s); \
+    case 16: return launch_one<F8V, 16, false>(xm, wm, ka, grid, cfg.smem, s); \
+    case 0: return launch_one<F8V, 0, false>(xm, wm, ka, grid, cfg.smem, s);   \
+    default: return launch_one<F8V, -1, false>(xm, wm, ka, grid, cfg.smem, s); \
     }
     if (f8) {
-        if (fw) return launch_one<true, true, false>(xm, wm, ka, grid, cfg.smem, s);
-        return launch_one<true, false, false>(xm, wm, ka, grid, cfg.smem, s);
+        BF_TC_WIN(true)
     }
-    if (fw) return launch_one<false, true, false>(xm, wm, ka, grid, cfg.smem, s);
-    return launch_one<false, false, false>(xm, wm, ka, grid, cfg.smem, s);
+    BF_TC_WIN(false)
+#undef BF_TC_WIN
 }
 
 }  // namespace bfi

@@ -301,6 +301,239 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Channel-looping weight kernel.  One thread per (beam, antenna column); a
+// block covers whole beams (32..256 threads per beam, up to two columns per
+// thread) and a run of channels.  On the fixed-point path the phase of each
+// (beam, antenna) advances by one exact 64-bit addition per channel, so the
+// per-(beam, antenna) table is read once per run of channels.  The reduced
+// phase is split into a 23-bit head (exact in FP32) and a 23-bit tail, and
+// the tail is applied as a first-order correction after sincospif, so the
+// FP32 weight is accurate to a few ulps relative to each component; the
+// near-boundary test then uses a relative window (1e-6) and the FP64
+// recomputation is rare.
+struct WGeom {
+    int N, B, b_pad, k_pad, n_cols;   // n_cols: stored antenna columns (K_pad / 2 or N)
+    int tpb, bpb, apt, cc;            // threads per beam, beams per block, columns per thread, channels per block
+    long long m_pad;
+};
+
+// twice the reduced phase as head + tail (head exact, |tail| <= 2^-22)
+__device__ __forceinline__ void split_fixed(unsigned long long ph, float &xh, float &xl)
+{
+    const long long sp = (long long)ph;
+    const int t = (int)(sp >> 41);                          // [-2^22, 2^22)
+    const unsigned u = (unsigned)(ph >> 18) & 0x7FFFFFu;   // next 23 bits
+    xh = (__int_as_float(0x4B400000 + t) - 12582912.0f) * 2.384185791015625e-07f;   // x 2^-22
+    xl = (__int_as_float(0x4B000000 | u) - 8388608.0f) * 2.842170943040401e-14f;    // x 2^-45
+}
+
+__device__ __forceinline__ void split_double(double x, float &xh, float &xl)
+{
+    xh = (float)x;
+    xl = (float)(x - (double)xh);
+}
+
+// exp(-i pi (xh + xl)) to a few FP32 ulps per component
+__device__ __forceinline__ float2 cis_neg(float xh, float xl)
+{
+    float s, c;
+    sincospif(xh, &s, &c);
+    const float d = 3.14159265358979f * xl;
+    return make_float2(fmaf(-d, s, c), -fmaf(d, c, s));
+}
+
+__device__ __noinline__ double2 cis_neg64(double x)
+{
+    double s, c;
+    sincospi(x, &s, &c);
+    return make_double2(c, -s);
+}
+
+template <int FMT>
+__device__ __forceinline__ void store_pair(void *w, const WGeom &g, int c, int b, int n, uint32_t qre_row,
+                                           uint32_t qim_row)
+{
+    using T2 = typename std::conditional<FMT == kFmtE4M3, uint16_t, uint32_t>::type;
+    const int mt = b / kBeamsPerMTile, bi = b % kBeamsPerMTile;
+    const long long row_re = (long long)mt * kRowsPerMTile + (bi >> 4) * 32 + (bi & 15);
+    T2 *base = reinterpret_cast<T2 *>(w);
+    const long long e_re = (((long long)c * g.m_pad + row_re) * g.k_pad) / 2 + n;
+    base[e_re] = (T2)qre_row;
+    base[e_re + (long long)16 * g.k_pad / 2] = (T2)qim_row;
+}
+
+template <int FMT, bool FIXED>
+__global__ void __launch_bounds__(256) k_weights2(const double *__restrict__ freqs, const double *__restrict__ tau,
+                                                  const unsigned long long *__restrict__ ab,
+                                                  const uint8_t *__restrict__ mask, WGeom g, int C,
+                                                  void *__restrict__ w, float *__restrict__ wscale,
+                                                  float *__restrict__ wsig)
+{
+    using Q = Quant<FMT>;
+    constexpr bool scaled = Q::qmax > 0.f;
+    __shared__ float red[8];
+    __shared__ int vote[8];
+    const int tid = threadIdx.x;
+    const int bl = tid / g.tpb, lt = tid % g.tpb;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.x * g.bpb + bl;
+    const int c0 = blockIdx.y * g.cc, c1 = min(C, c0 + g.cc);
+    const bool in_block = bl < g.bpb && b < g.b_pad;
+    unsigned long long ph[2] = {0ull, 0ull}, dph[2] = {0ull, 0ull};
+    bool live[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int n = lt + a * g.tpb;
+        live[a] = in_block && a < g.apt && n < g.N && b < g.B && !(mask && !mask[n]);
+        if (FIXED && live[a]) {
+            const size_t i = (size_t)b * g.N + n;
+            dph[a] = ab[2 * i + 1];
+            ph[a] = ab[2 * i] + (unsigned long long)c0 * dph[a];
+        }
+    }
+    for (int c = c0; c < c1; ++c) {
+        float2 v[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            v[a] = make_float2(0.f, 0.f);
+            if (live[a]) {
+                float xh, xl;
+                if (FIXED) split_fixed(ph[a], xh, xl);
+                else {
+                    const double p2 = freqs[c] * tau[(size_t)b * g.N + lt + a * g.tpb];
+                    split_double(2.0 * (p2 - rint(p2)), xh, xl);
+                }
+                v[a] = cis_neg(xh, xl);
+            }
+        }
+        float sig = 1.f;
+        if (scaled) {
+            float mx = 0.f;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) mx = fmaxf(mx, fmaxf(fabsf(v[a].x), fabsf(v[a].y)));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (g.tpb > 32) {   // beams span several warps
+                if (lane == 0) red[warp] = mx;
+                __syncthreads();
+                const int w0 = (bl * g.tpb) >> 5, nw = g.tpb >> 5;
+                for (int k = 0; k < nw; ++k) mx = fmaxf(mx, red[w0 + k]);
+                __syncthreads();
+            }
+            if (mx > 0.f) sig = mx / Q::qmax;
+        }
+        // quantise, store, note components within the FP32 error of a boundary
+        bool near_any = false;
+        uint32_t near_bits = 0;
+        if (in_block) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int n = lt + a * g.tpb;
+                if (a >= g.apt || n >= g.n_cols) continue;
+                float re = v[a].x, im = v[a].y;
+                if (scaled) {
+                    re /= sig;
+                    im /= sig;
+                }
+                bool near = false;
+                if (live[a]) {
+                    const float dre = 1e-6f * fabsf(re) + 1e-12f, dim = 1e-6f * fabsf(im) + 1e-12f;
+                    near = !pair_same<Q>(Q::q2(re - dre, re + dre)) || !pair_same<Q>(Q::q2(im - dim, im + dim));
+                }
+                store_pair<FMT>(w, g, c, b, n, Q::q2(re, -im), Q::q2(im, re));
+                near_bits |= (uint32_t)near << a;
+                near_any |= near;
+            }
+        }
+        if (!scaled) {
+            // unscaled formats: recompute just the flagged components in FP64
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                if (near_bits & (1u << a)) {
+                    const int n = lt + a * g.tpb;
+                    double x;
+                    if (FIXED) {
+                        x = (double)(long long)ph[a] * 1.0842021724855044e-19;   // x 2^-63
+                    } else {
+                        const double p2 = freqs[c] * tau[(size_t)b * g.N + n];
+                        x = 2.0 * (p2 - rint(p2));
+                    }
+                    const double2 d = cis_neg64(x);
+                    const uint32_t lo = Q::q(d.x), hi = Q::q(-d.y), lo2 = Q::q(d.y);
+                    constexpr int sh = 8 * sizeof(typename Q::T);
+                    store_pair<FMT>(w, g, c, b, n, lo | (hi << sh), lo2 | (lo << sh));
+                }
+        } else {
+            // scaled formats: the scale depends on every antenna of the beam, so a
+            // flagged beam is recomputed whole in FP64
+            bool redo = __any_sync(0xffffffffu, near_any);
+            if (g.tpb > 32) {
+                if (lane == 0) vote[warp] = redo;
+                __syncthreads();
+                const int w0 = (bl * g.tpb) >> 5, nw = g.tpb >> 5;
+                redo = false;
+                for (int k = 0; k < nw; ++k) redo |= vote[w0 + k] != 0;
+                __syncthreads();
+            }
+            if (redo) {   // uniform across the beam (and across the warp when tpb <= 32)
+                double2 d[2];
+                double mx = 0.0;
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    d[a] = make_double2(0.0, 0.0);
+                    if (live[a]) {
+                        double x;
+                        if (FIXED) {
+                            x = (double)(long long)ph[a] * 1.0842021724855044e-19;
+                        } else {
+                            const double p2 = freqs[c] * tau[(size_t)b * g.N + lt + a * g.tpb];
+                            x = 2.0 * (p2 - rint(p2));
+                        }
+                        d[a] = cis_neg64(x);
+                    }
+                    mx = fmax(mx, fmax(fabs(d[a].x), fabs(d[a].y)));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                // tpb > 32 with a redo is handled below through shared memory
+                __shared__ double redd[8];
+                if (g.tpb > 32) {
+                    if (lane == 0) redd[warp] = mx;
+                    __syncwarp();
+                }
+                if (g.tpb > 32) {
+                    // only warps of redo beams reach here; they synchronise among
+                    // themselves through a named barrier of the beam's threads
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + bl), "r"(g.tpb) : "memory");
+                    const int w0 = (bl * g.tpb) >> 5, nw = g.tpb >> 5;
+                    for (int k = 0; k < nw; ++k) mx = fmax(mx, redd[w0 + k]);
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + bl), "r"(g.tpb) : "memory");
+                }
+                const double sig64 = mx > 0.0 ? mx / (double)Q::qmax : 1.0;
+                if (in_block) {
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        const int n = lt + a * g.tpb;
+                        if (a >= g.apt || n >= g.n_cols) continue;
+                        const double re = d[a].x / sig64, im = d[a].y / sig64;
+                        const uint32_t qre = Q::q(re), qim = Q::q(im), qimn = Q::q(-im);
+                        constexpr int sh = 8 * sizeof(typename Q::T);
+                        store_pair<FMT>(w, g, c, b, n, qre | (qimn << sh), qim | (qre << sh));
+                    }
+                }
+                sig = (float)sig64;
+            }
+        }
+        if (in_block && lt == 0) {
+            wscale[(size_t)c * g.b_pad + b] = sig * sig;
+            wsig[(size_t)c * g.b_pad + b] = sig;
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) ph[a] += dph[a];
+    }
+}
+
 // Decode the stored weights back to complex float32 [C][B][N] (without scale).
 template <int FMT>
 __global__ void k_export(const void *__restrict__ w, const float *__restrict__ wsig, int C, int N, int B,
@@ -359,8 +592,44 @@ cudaError_t launch_delays(bf_plan *p, cudaStream_t s)
 }
 
 template <bool FIXED>
+static bool weights2_launch(bf_plan *p, cudaStream_t s)
+{
+    const WeightFormat &f = p->wf;
+    if (f.simt) return false;
+    WGeom g;
+    g.N = p->N;
+    g.B = p->B;
+    g.b_pad = f.b_pad;
+    g.k_pad = f.k_pad;
+    g.n_cols = f.k_pad / 2;
+    g.m_pad = f.m_pad;
+    if (g.n_cols > 512) return false;
+    g.tpb = g.n_cols <= 32 ? 32 : g.n_cols <= 64 ? 64 : g.n_cols <= 128 ? 128 : 256;
+    g.bpb = 256 / g.tpb;
+    g.apt = (g.n_cols + g.tpb - 1) / g.tpb;
+    const int beam_blocks = (g.b_pad + g.bpb - 1) / g.bpb;
+    // enough blocks to fill the GPU a few times over, each running many channels
+    const int target = 8 * p->num_sms * (2048 / 256);
+    int chunks = std::max(1, std::min(p->C, (target + beam_blocks - 1) / beam_blocks));
+    g.cc = (p->C + chunks - 1) / chunks;
+    chunks = (p->C + g.cc - 1) / g.cc;
+    dim3 grid(beam_blocks, chunks);
+#define BF_W2(F) k_weights2<F, FIXED><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_ab, p->d_mask, g, p->C, \
+                                                           p->d_w, p->d_wscale, p->d_wsig)
+    switch (fmt_code(p)) {
+    case kFmtF16: BF_W2(kFmtF16); break;
+    case kFmtBF16: BF_W2(kFmtBF16); break;
+    case kFmtE4M3: BF_W2(kFmtE4M3); break;
+    default: BF_W2(kFmtI8); break;
+    }
+#undef BF_W2
+    return true;
+}
+
+template <bool FIXED>
 static void weights_launch(bf_plan *p, cudaStream_t s)
 {
+    if (weights2_launch<FIXED>(p, s)) return;
     dim3 grid((p->wf.b_pad + 7) / 8, p->C);
     const WeightFormat &f = p->wf;
 #define BF_W_LAUNCH(F)                                                                                      \

@@ -49,15 +49,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  : "memory");
 }
 
+// Test the phase; if it is not complete the thread may sleep until it
+// completes or the suspend-time hint (1 ms) elapses, so waiting warps do not
+// spin on the issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000000u)
         : "memory");
     return ok != 0;
 }
@@ -69,9 +72,7 @@ enum : unsigned { kErrTimeout = 1u };
 // `limit_cycles` SM clock cycles (about 1 s per 2e9 at the maximum clock).
 // On timeout, record it in *err, raise the CTA-wide abort flag and return
 // false.  Also returns false once another role of the CTA has raised the
-// abort flag.  The abort flag and the cycle counter are read only every 64
-// polls: try_wait itself suspends the thread for a while when the phase is
-// not complete, so a poll is cheap but not free.
+// abort flag.  The abort flag and the cycle counter are read every 8 polls.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                           unsigned *err, uint64_t limit_cycles)
 {
@@ -79,7 +80,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 0) {
+        if ((i & 7u) == 0) {
             if (*abort_flag) return false;
             if ((uint64_t)(clock64() - t0) > limit_cycles) {
                 *abort_flag = 1;
