@@ -20,13 +20,14 @@
 //                128 x NT x 16 (or x32 for FP8) per instruction, into two
 //                NT-column FP32 accumulators (the epilogue drains one while
 //                the next tile accumulates)
-//   warps 2-17   epilogue, four warps per TMEM lane quarter, each on a slice
-//                of the tile's columns: the slice is read with 64-column
+//   warps 2-9    epilogue, two warps per TMEM lane quarter, each on a half
+//                of the tile's columns: the half is read with 128-column
 //                tcgen05.ld and the accumulator handed back to the MMA before
-//                any arithmetic; then squares, window sums in a fixed order,
-//                re+im combination via one shuffle (the two rows of a beam
-//                are 16 lanes apart), window powers staged in shared memory
-//   warp 18      store warp: writes each staged tile as one run of windows
+//                any arithmetic; then squares with packed FP32 FMAs, window
+//                sums in a fixed order, re+im combination via one shuffle (the
+//                two rows of a beam are 16 lanes apart), window powers staged
+//                in shared memory
+//   warp 10      store warp: writes each staged tile as one run of windows
 //                per beam (16-byte stores), four tiles in flight.
 // Work: the M tiles of a channel are split into weight groups; the CTAs are
 // arranged as P sets of Gq CTAs, the CTAs of one set hold different groups
@@ -46,7 +47,7 @@
 
 namespace bfi {
 
-constexpr int kEpiWarps = 16;
+constexpr int kEpiWarps = 8;
 constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
 constexpr int kTcThreads = (3 + kEpiWarps) * 32;
 constexpr int kStageDepth = 4;                     // staged tiles in flight
@@ -117,6 +118,17 @@ __device__ __forceinline__ float sumsq64(const float *v)
 #pragma unroll
         for (int j = 0; j < 8; ++j) s[j] = fmaf(v[i + j], v[i + j], s[j]);
     return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+// Sum of squares of n (multiple of 8) raw FP32 values with packed FMAs in
+// four independent chains, combined in a fixed order.
+template <int n>
+__device__ __forceinline__ float sumsq_pk(const uint32_t *r)
+{
+    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) sq_acc2(acc[i & 3], r[2 * i], r[2 * i + 1]);
+    return (sum2(acc[0]) + sum2(acc[1])) + (sum2(acc[2]) + sum2(acc[3]));
 }
 
 // WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
@@ -396,25 +408,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 }
                             }
                         };
-                        const int n64 = cols / 64, rem = cols % 64;   // rem is a multiple of 16
-                        for (int bt = 0; bt < n64; ++bt) {
-                            float v[64];
-                            tmem_ld64(taddr + bt * 64, v);
-                            if (bt == n64 - 1 && rem == 0) release();
-                            if (WIN == 64) {
-                                emit(sumsq64(v));
-                            } else if (WIN == 32) {
-                                emit(sumsq32(v));
-                                emit(sumsq32(v + 32));
-                            } else if (WIN == 16) {
+                        int col = 0;
+                        if (WIN > 0 && cols % 128 == 0) {
+                            // 128 columns per load; the accumulator is released after the
+                            // last load, before the squares are summed
+                            for (; col < cols; col += 128) {
+                                uint32_t r[128];
+                                tmem_ld128(taddr + col, r);
+                                if (col + 128 == cols) release();
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) emit(sumsq16(v + 16 * k));
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) add16(v + 16 * k);
+                                for (int k = 0; k < 128 / (WIN > 0 ? WIN : 128); ++k)
+                                    emit(sumsq_pk<(WIN > 0 ? WIN : 128)>(r + k * (WIN > 0 ? WIN : 128)));
                             }
                         }
-                        for (int col = n64 * 64; col < cols; col += 16) {
+                        const int n64 = (cols - col) / 64, rem = (cols - col) % 64;   // rem is a multiple of 16
+                        for (int bt = 0; bt < n64; ++bt) {
+                            float v[64];
+                            tmem_ld64(taddr + col + bt * 64, v);
+                            if (bt == n64 - 1 && rem == 0) release();
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) add16(v + 16 * k);
+                        }
+                        for (col += n64 * 64; col < cols; col += 16) {
                             float v[16];
                             tmem_ld16(taddr + col, v);
                             if (col + 16 == cols) release();
@@ -547,7 +562,7 @@ bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
         TcConfig c;
         c.nt = nt;
         c.nsplit = 1;
-        for (int ns : {4, 2}) {
+        for (int ns : {2}) {
             const int w = nt / ns;
             if (nt % ns == 0 && w % 16 == 0 && w % t_int == 0) {
                 c.nsplit = ns;
