@@ -189,6 +189,23 @@ const char *bf_last_error(void);
 bf_status bf_plan_set_kernel(bf_plan *plan, int kernel, int tile_t);
 
 /*
+ * bf_plan_set_tiles — tensor-core tiling (each 0 = automatic):
+ *  tile_t       samples per tile (MMA N), as in bf_plan_set_kernel;
+ *  group_tiles  128-row weight tiles (64 beams each) kept resident in shared
+ *               memory while a CTA walks along time (1..16);
+ *  x_stages     voltage tiles in flight (2..4).
+ * The autotuner (paper_1412_4907_gb300.tune) searches these.  No effect on
+ * BF_C32 plans.  Errors: BF_ERR_ARG for out-of-range values,
+ * BF_ERR_UNSUPPORTED if the combination does not fit in shared memory.
+ */
+bf_status bf_plan_set_tiles(bf_plan *plan, int tile_t, int group_tiles, int x_stages);
+
+/* bf_plan_query_tiles — the tiling in use (any output may be NULL): tile_t,
+ * group_tiles, x_stages and the number of weight groups per channel. */
+bf_status bf_plan_query_tiles(const bf_plan *plan, int *tile_t, int *group_tiles,
+                              int *x_stages, int *n_groups);
+
+/*
  * bf_plan_set_input_order — the antenna order of the voltage stream differs
  * from the array order of pos_m/mask (the F-engine lookup table of Section 3):
  * array antenna n arrives in input slot perm[n] (host [N] ints, a permutation

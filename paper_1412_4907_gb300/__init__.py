@@ -43,6 +43,8 @@ SIGNATURES = {
     "bf_last_error": [],
     "bf_plan_set_kernel": [_P, _I, _I],
     "bf_plan_set_input_order": [_P, _P],
+    "bf_plan_set_tiles": [_P, _I, _I, _I],
+    "bf_plan_query_tiles": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "bf_plan_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_S)],
     "bf_export_weights": [_P, _P, _P],
     "bf_corner_turn": [_P, _I, _P, _I, _I, _I, _I, _P, _P],
@@ -129,6 +131,16 @@ def bf_last_error() -> str:
 
 def bf_plan_set_kernel(plan: int, kernel: int, tile_t: int = 0):
     _check(_lib.bf_plan_set_kernel(plan, kernel, tile_t))
+
+
+def bf_plan_set_tiles(plan: int, tile_t: int = 0, group_tiles: int = 0, x_stages: int = 0):
+    _check(_lib.bf_plan_set_tiles(plan, tile_t, group_tiles, x_stages))
+
+
+def bf_plan_query_tiles(plan: int) -> dict:
+    t, g, x, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.bf_plan_query_tiles(plan, ctypes.byref(t), ctypes.byref(g), ctypes.byref(x), ctypes.byref(n)))
+    return {"tile_t": t.value, "group_tiles": g.value, "x_stages": x.value, "n_groups": n.value}
 
 
 def bf_plan_set_input_order(plan: int, perm=None):
@@ -228,6 +240,12 @@ class Plan:
 
     def set_kernel(self, kernel: int, tile_t: int = 0):
         bf_plan_set_kernel(self.handle, kernel, tile_t)
+
+    def set_tiles(self, tile_t: int = 0, group_tiles: int = 0, x_stages: int = 0):
+        bf_plan_set_tiles(self.handle, tile_t, group_tiles, x_stages)
+
+    def query_tiles(self) -> dict:
+        return bf_plan_query_tiles(self.handle)
 
     def set_input_order(self, perm):
         bf_plan_set_input_order(self.handle, perm)

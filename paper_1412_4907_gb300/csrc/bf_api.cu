@@ -118,7 +118,7 @@ static bool choose_format(bf_plan *p, std::string *why)
                "16-bit and integer modes, N % 8 == 0 for FP8)";
         return false;
     }
-    return tc_choose(p, p->tile_req, &p->tc, why);
+    return tc_choose(p, p->tc_req, &p->tc, why);
 }
 
 extern "C" {
@@ -451,18 +451,30 @@ bf_status bf_plan_set_kernel(bf_plan *p, int kernel, int tile_t)
 {
     g_last_error.clear();
     if (!p) return set_error(BF_ERR_ARG, "plan is NULL");
+    if (kernel < BF_KERNEL_AUTO || kernel > BF_KERNEL_TC) return set_error(BF_ERR_ARG, "unknown kernel");
     if (kernel == BF_KERNEL_SIMT && p->dtype != BF_C32)
         return set_error(BF_ERR_UNSUPPORTED, "the SIMT kernel runs only BF_C32");
     if (kernel == BF_KERNEL_TC && p->dtype == BF_C32)
         return set_error(BF_ERR_UNSUPPORTED, "the tensor-core kernel does not run BF_C32");
-    if (kernel < BF_KERNEL_AUTO || kernel > BF_KERNEL_TC) return set_error(BF_ERR_ARG, "unknown kernel");
-    if (!p->wf.simt) {
-        TcConfig cfg;
-        std::string why;
-        if (!tc_choose(p, tile_t, &cfg, &why)) return set_error(BF_ERR_UNSUPPORTED, why);
-        p->tc = cfg;
-        p->tile_req = tile_t;
-    }
+    return bf_plan_set_tiles(p, tile_t, p->tc_req.group_tiles, p->tc_req.x_stages);
+}
+
+bf_status bf_plan_set_tiles(bf_plan *p, int tile_t, int group_tiles, int x_stages)
+{
+    g_last_error.clear();
+    if (!p) return set_error(BF_ERR_ARG, "plan is NULL");
+    if (tile_t < 0 || group_tiles < 0 || group_tiles > 16 || x_stages < 0 || x_stages == 1 || x_stages > 4)
+        return set_error(BF_ERR_ARG, "tile_t >= 0, 0 <= group_tiles <= 16, x_stages in {0, 2, 3, 4}");
+    if (p->wf.simt) return BF_OK;   // the SIMT kernel has a fixed tiling
+    TcRequest req;
+    req.tile_t = tile_t;
+    req.group_tiles = group_tiles;
+    req.x_stages = x_stages;
+    TcConfig cfg;
+    std::string why;
+    if (!tc_choose(p, req, &cfg, &why)) return set_error(BF_ERR_UNSUPPORTED, why);
+    p->tc = cfg;
+    p->tc_req = req;
     return BF_OK;
 }
 
@@ -474,6 +486,18 @@ bf_status bf_plan_query(const bf_plan *p, int *kernel, int *tile_t, int *group_t
     if (tile_t) *tile_t = p->wf.simt ? 64 : p->tc.nt;
     if (group_tiles) *group_tiles = p->wf.simt ? 0 : p->tc.group;
     if (device_bytes) *device_bytes = p->dev_bytes;
+    return BF_OK;
+}
+
+bf_status bf_plan_query_tiles(const bf_plan *p, int *tile_t, int *group_tiles, int *x_stages, int *n_groups)
+{
+    g_last_error.clear();
+    if (!p) return set_error(BF_ERR_ARG, "plan is NULL");
+    const bool s = p->wf.simt;
+    if (tile_t) *tile_t = s ? 64 : p->tc.nt;
+    if (group_tiles) *group_tiles = s ? 0 : p->tc.group;
+    if (x_stages) *x_stages = s ? 0 : p->tc.xst;
+    if (n_groups) *n_groups = s ? 0 : p->tc.n_groups;
     return BF_OK;
 }
 

@@ -35,9 +35,17 @@ struct WeightFormat {
     float qmax = 0.f;    // > 0: per-beam scale sigma_b = max|component| / qmax
 };
 
+// Requested tensor-core tiling (0 = choose automatically).
+struct TcRequest {
+    int tile_t = 0;      // samples per tile (MMA N)
+    int group_tiles = 0; // M tiles whose weights stay resident
+    int x_stages = 0;    // voltage tiles in flight
+};
+
 // Tensor-core launch configuration.
 struct TcConfig {
     int nt = 256;        // time-tile (MMA N)
+    int xst = 2;         // voltage stages in flight
     int nsplit = 2;      // epilogue column halves
     int group = 1;       // M tiles whose weights stay resident per work unit
     int n_groups = 1;
@@ -61,7 +69,7 @@ bf_status cuda_error(cudaError_t e, const char *what);
 struct bf_plan {
     int N = 0, C = 0, B = 0, dtype = 0, t_int = 1, layout = 0;
     int kernel = BF_KERNEL_AUTO;
-    int tile_req = 0;
+    bfi::TcRequest tc_req;
     int num_sms = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -113,7 +121,7 @@ cudaError_t launch_simt_range(bf_plan *p, const void *x, int c_base, int c_launc
                               int complex_out, cudaStream_t s);
 
 // k_tc.cu
-bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why);
+bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why);
 cudaError_t launch_tc(bf_plan *p, const TcArgs &a, cudaStream_t s, std::string *why);
 
 // k_aux.cu

@@ -53,13 +53,14 @@ constexpr int kTcThreads = (3 + kEpiWarps) * 32;
 constexpr int kStageDepth = 4;                     // staged tiles in flight
 constexpr int kTmemCols = 512;
 constexpr int kMaxWinPerTile = 16;
+constexpr int kMaxXStages = 4;
 constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
 
 struct TcKernelArgs {
     long long ct_total;                 // channels x time tiles
     int n_groups, g_base, g_rem, gmax;  // weight groups of M tiles
     int gq;                             // CTAs per set (distinct groups walked in step)
-    int t_tiles, nt, kb, ke, nsplit, wpt;
+    int t_tiles, nt, kb, ke, nsplit, wpt, xst;   // xst: voltage stages in flight
     int c_base, c_total, T, T_o, t_int, B, b_pad;
     uint32_t idesc;
     uint32_t x_stage_bytes, w_slot_bytes;
@@ -142,28 +143,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t sx = base;
-    const uint32_t sw = sx + 2 * a.x_stage_bytes;
-    float *stage = reinterpret_cast<float *>(gbase + 2 * a.x_stage_bytes + a.gmax * a.w_slot_bytes);
+    const uint32_t sw = sx + a.xst * a.x_stage_bytes;
+    float *stage = reinterpret_cast<float *>(gbase + a.xst * a.x_stage_bytes + a.gmax * a.w_slot_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
-    const uint32_t b_xfull = smem_u32(bars + 0);
-    const uint32_t b_xempty = smem_u32(bars + 2);
-    const uint32_t b_tfull = smem_u32(bars + 4);
-    const uint32_t b_tempty = smem_u32(bars + 6);
-    const uint32_t b_drain = smem_u32(bars + 8);
-    const uint32_t b_wfull = smem_u32(bars + 9);
-    const uint32_t b_wempty = smem_u32(bars + 9 + a.gmax);
-    const uint32_t b_sfull = smem_u32(bars + 9 + 2 * a.gmax);   // [stage]: every slice staged
-    const uint32_t b_sempty = b_sfull + 8 * kStageDepth;         // [stage]: written out
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 9 + 2 * a.gmax + 2 * kStageDepth);
+    const uint32_t b_xfull = smem_u32(bars + 0);                 // [kMaxXStages]
+    const uint32_t b_xempty = smem_u32(bars + kMaxXStages);      // [kMaxXStages]
+    const uint32_t b_tfull = smem_u32(bars + 2 * kMaxXStages);   // [2]
+    const uint32_t b_tempty = b_tfull + 16;                       // [2]
+    const uint32_t b_drain = b_tfull + 32;
+    const uint32_t b_wfull = b_drain + 8;                         // [gmax]
+    const uint32_t b_wempty = b_wfull + 8 * a.gmax;               // [gmax]
+    const uint32_t b_sfull = b_wempty + 8 * a.gmax;               // [stage]: every slice staged
+    const uint32_t b_sempty = b_sfull + 8 * kStageDepth;          // [stage]: written out
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 5 + 2 * a.gmax + 2 * kStageDepth);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < a.xst; ++i) {
             mbar_init(b_xfull + 8 * i, 1);
             mbar_init(b_xempty + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
             mbar_init(b_tempty + 8 * i, kEpiWarps);
         }
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int kb = 0; kb < a.kb; ++kb)
                         tma_load_3d(sx + xs * a.x_stage_bytes + kb * a.nt * 128, &xmap, b_xfull + 8 * xs,
                                     kb * a.ke, tt * a.nt, c);
-                    xs ^= 1;
+                    if (++xs == a.xst) xs = 0;
                     if (ct == ct0 || tt == 0) {   // weights of (group, channel)
                         for (int s = 0; s < gs; ++s) {
                             if (!mbar_wait(b_wempty + 8 * s, ((wcnt >> s) & 1u) ^ 1u, abort_flag, a.err,
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
             if (*abort_flag) {   // let every issued copy land before the CTA exits
-                for (int i = 0; i < 2; ++i)
+                for (int i = 0; i < a.xst; ++i)
                     if (x_issued & (1u << i)) drain_wait(b_xfull + 8 * i, ((xcnt >> i) & 1u) ^ 1u);
                 for (int s = 0; s < a.gmax; ++s)
                     if (w_issued & (1u << s)) drain_wait(b_wfull + 8 * s, ((wcnt >> s) & 1u) ^ 1u);
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     if (!ok) break;
                     mma_commit(b_xempty + 8 * xs);
-                    xs ^= 1;
+                    if (++xs == a.xst) xs = 0;
                     if (++tt == a.t_tiles) tt = 0;
                 }
             }
@@ -542,10 +545,10 @@ static int gcd_i(int x, int y)
     return x;
 }
 
-static int ctrl_bytes() { return 8 * (9 + 2 * 16 + 2 * kStageDepth) + 16; }
+static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 5 + 2 * 16 + 2 * kStageDepth) + 16; }
 static int stage_bytes() { return kStageDepth * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
 
-bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
+bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why)
 {
     const WeightFormat &f = p->wf;
     const int t_int = p->t_int;
@@ -557,35 +560,46 @@ bool tc_choose(bf_plan *p, int tile_req, TcConfig *cfg, std::string *why)
     const int mt = f.m_pad / kRowsPerMTile;
     for (int nt = 256; nt >= (int)unit; nt -= 16) {
         if (nt % unit) continue;
-        if (tile_req && nt != tile_req) continue;
+        if (req.tile_t && nt != req.tile_t) continue;
         if (nt / t_int > kMaxWinPerTile) continue;   // staged window powers per tile
-        TcConfig c;
-        c.nt = nt;
-        c.nsplit = 1;
-        for (int ns : {2}) {
-            const int w = nt / ns;
-            if (nt % ns == 0 && w % 16 == 0 && w % t_int == 0) {
-                c.nsplit = ns;
-                break;
-            }
-        }
-        c.fast_windows = (t_int % 16) == 0;
         const int x_stage = f.kb * nt * 128;
         const int w_slot = f.kb * 16384;
-        const int fixed = 2 * x_stage + stage_bytes() + ctrl_bytes() + 1024;
-        const int avail = kSmemLimit - fixed;
-        if (avail < w_slot) continue;
-        int g = std::min(mt, std::min(16, avail / w_slot));
-        c.n_groups = (mt + g - 1) / g;
-        const int g_base = mt / c.n_groups, g_rem = mt % c.n_groups;
-        c.group = g_base + (g_rem ? 1 : 0);
-        c.smem = fixed + c.group * w_slot;
-        c.smem = std::max(c.smem, 116 * 1024);   // one CTA per SM: it owns all 512 TMEM columns
-        *cfg = c;
+        // default: the fewest weight groups per channel (each group re-reads the
+        // voltage tile), then the most voltage stages in flight; a request fixes
+        // the stage count and/or the group size
+        bool found = false;
+        TcConfig best;
+        for (int xst = kMaxXStages; xst >= 2; --xst) {
+            if (req.x_stages && xst != req.x_stages) continue;
+            const int fixed = xst * x_stage + stage_bytes() + ctrl_bytes() + 1024;
+            const int avail = kSmemLimit - fixed;
+            if (avail < w_slot) continue;
+            int g = std::min(mt, std::min(16, avail / w_slot));
+            if (req.group_tiles) {
+                if (req.group_tiles > g) continue;
+                g = req.group_tiles;
+            }
+            TcConfig c;
+            c.nt = nt;
+            c.xst = xst;
+            c.nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
+            c.fast_windows = (t_int % 16) == 0;
+            c.n_groups = (mt + g - 1) / g;
+            const int g_base = mt / c.n_groups, g_rem = mt % c.n_groups;
+            c.group = g_base + (g_rem ? 1 : 0);
+            c.smem = std::max(fixed + c.group * w_slot, 116 * 1024);   // one CTA per SM: it owns all TMEM
+            if (!found || c.n_groups < best.n_groups) {
+                best = c;
+                found = true;
+            }
+        }
+        if (!found) continue;
+        *cfg = best;
         return true;
     }
-    *why = tile_req ? "requested tile does not fit the tensor-core kernel"
-                    : "antenna count too large for the resident-weight tensor-core kernel";
+    *why = (req.tile_t || req.x_stages || req.group_tiles)
+               ? "requested tile configuration does not fit the tensor-core kernel"
+               : "antenna count too large for the resident-weight tensor-core kernel";
     return false;
 }
 
@@ -651,6 +665,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.ke = f.ke;
     ka.nsplit = cfg.nsplit;
     ka.wpt = cfg.nt / ta.t_int;
+    ka.xst = cfg.xst;
     ka.c_base = ta.c_base;
     ka.c_total = ta.c_total;
     ka.T = ta.T;
