@@ -54,6 +54,7 @@ constexpr int kStageDepth = 4;                     // staged tiles in flight
 constexpr int kTmemCols = 512;
 constexpr int kMaxWinPerTile = 16;
 constexpr int kMaxXStages = 4;
+constexpr int kMaxAcc = 8;                         // TMEM accumulators (512 columns / tile)
 constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
 
 struct TcKernelArgs {
@@ -61,6 +62,7 @@ struct TcKernelArgs {
     int n_groups, g_base, g_rem, gmax;  // weight groups of M tiles
     int gq;                             // CTAs per set (distinct groups walked in step)
     int t_tiles, nt, kb, ke, nsplit, wpt, xst;   // xst: voltage stages in flight
+    int nacc;                                    // TMEM accumulators in flight
     int c_base, c_total, T, T_o, t_int, B, b_pad;
     uint32_t idesc;
     uint32_t x_stage_bytes, w_slot_bytes;
@@ -148,14 +150,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
     const uint32_t b_xfull = smem_u32(bars + 0);                 // [kMaxXStages]
     const uint32_t b_xempty = smem_u32(bars + kMaxXStages);      // [kMaxXStages]
-    const uint32_t b_tfull = smem_u32(bars + 2 * kMaxXStages);   // [2]
-    const uint32_t b_tempty = b_tfull + 16;                       // [2]
-    const uint32_t b_drain = b_tfull + 32;
+    const uint32_t b_tfull = smem_u32(bars + 2 * kMaxXStages);   // [kMaxAcc]
+    const uint32_t b_tempty = b_tfull + 8 * kMaxAcc;              // [kMaxAcc]
+    const uint32_t b_drain = b_tempty + 8 * kMaxAcc;
     const uint32_t b_wfull = b_drain + 8;                         // [gmax]
     const uint32_t b_wempty = b_wfull + 8 * a.gmax;               // [gmax]
     const uint32_t b_sfull = b_wempty + 8 * a.gmax;               // [stage]: every slice staged
     const uint32_t b_sempty = b_sfull + 8 * kStageDepth;          // [stage]: written out
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 5 + 2 * a.gmax + 2 * kStageDepth);
+    uint32_t *tmem_holder =
+        reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * a.gmax + 2 * kStageDepth);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(b_xfull + 8 * i, 1);
             mbar_init(b_xempty + 8 * i, 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < a.nacc; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
             mbar_init(b_tempty + 8 * i, kEpiWarps);
         }
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             }
                         mma_commit(b_tfull + 8 * acc);
                         if (lastw) mma_commit(b_wempty + 8 * s);
-                        acc ^= 1;
+                        if (++acc == a.nacc) acc = 0;
                     }
                     if (!ok) break;
                     mma_commit(b_xempty + 8 * xs);
@@ -412,7 +415,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             }
                         };
                         int col = 0;
-                        if (WIN > 0 && cols % 128 == 0) {
+                        if (WIN > 0 && cols == 64) {
+                            uint32_t r[64];
+                            tmem_ld64r(taddr, r);
+                            release();
+#pragma unroll
+                            for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
+                                emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
+                            col = 64;
+                        } else if (WIN > 0 && cols % 128 == 0) {
                             // 128 columns per load; the accumulator is released after the
                             // last load, before the squares are summed
                             for (; col < cols; col += 128) {
@@ -441,7 +452,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(b_sfull + 8 * sb);   // publishes the staged windows
                     }
-                    acc ^= 1;
+                    if (++acc == a.nacc) acc = 0;
                 }
                 if (++tt == a.t_tiles) {
                     tt = 0;
@@ -545,7 +556,7 @@ static int gcd_i(int x, int y)
     return x;
 }
 
-static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 5 + 2 * 16 + 2 * kStageDepth) + 16; }
+static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * 16 + 2 * kStageDepth) + 16; }
 static int stage_bytes() { return kStageDepth * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
 
 bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why)
@@ -666,6 +677,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.nsplit = cfg.nsplit;
     ka.wpt = cfg.nt / ta.t_int;
     ka.xst = cfg.xst;
+    ka.nacc = std::min(kMaxAcc, kTmemCols / cfg.nt);
     ka.c_base = ta.c_base;
     ka.c_total = ta.c_total;
     ka.T = ta.T;
