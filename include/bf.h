@@ -245,6 +245,31 @@ bf_status bf_corner_turn(const void *d_in, int in_dtype, void *d_out, int out_dt
                          int n_ant, int n_chan, int n_samp, const int *perm,
                          void *stream);
 
+/*
+ * bf_execute_nct_static — bf_execute for an antenna-major (BF_LAYOUT_NCT)
+ * tensor-core plan that allocates nothing.  The paper has no counterpart: it
+ * exists for callers that cannot allocate device memory when they execute
+ * (allocators that forbid cudaMalloc after set-up, real-time loops that must
+ * not pay for an allocation or the synchronisation of freeing one, processes
+ * with a fixed memory budget).  bf_execute lays the corner-turned voltages out
+ * in plan scratch that it allocates (and grows) on first use; this call uses
+ * a fixed 64 MiB array in device memory instead, which every GPU that loads
+ * the library holds until the process exits.
+ *  d_voltages, n_samp, d_power, stream: as bf_execute.  The corner-turned
+ *  input, C * n_samp * N samples of the plan's dtype (plus 4 bytes per sample
+ *  for BF_CI8 / BF_CI4), must fit in the 64 MiB; larger inputs return
+ *  BF_ERR_ARG without doing anything.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other plans,
+ * other threads) race on it and must be serialised by the caller.  Nothing in
+ * it needs to start at zero.  Errors: BF_ERR_UNSUPPORTED for a CTN or FP32
+ * plan; otherwise as bf_execute.
+ */
+bf_status bf_execute_nct_static(bf_plan *plan, const void *d_voltages, int n_samp,
+                                float *d_power, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,7 @@ SIGNATURES = {
     "bf_plan_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_S)],
     "bf_export_weights": [_P, _P, _P],
     "bf_corner_turn": [_P, _I, _P, _I, _I, _I, _I, _P, _P],
+    "bf_execute_nct_static": [_P, _P, _I, _P, _P],
 }
 
 
@@ -115,6 +116,10 @@ def bf_execute_incoherent(plan: int, d_voltages: int, n_samp: int, d_power: int,
 
 def bf_execute_host(plan: int, h_voltages: int, n_samp: int, h_power: int):
     _check(_lib.bf_execute_host(plan, h_voltages, n_samp, h_power))
+
+
+def bf_execute_nct_static(plan: int, d_voltages: int, n_samp: int, d_power: int, stream: int = 0):
+    _check(_lib.bf_execute_nct_static(plan, d_voltages, n_samp, d_power, stream or None))
 
 
 def bf_sync(plan: int):

@@ -1,0 +1,95 @@
+// bf_execute_nct_static: the antenna-major execute path (corner turn, then
+// the tensor-core beamformer) with its scratch in a fixed device array
+// instead of memory the plan allocates.
+//
+// Some callers cannot allocate device memory at the time they execute: code
+// running under an allocator that forbids cudaMalloc outside set-up, real-time
+// loops where an allocation (and the device-wide synchronisation that freeing
+// the old buffer needs) would break the latency budget, or processes whose
+// memory is budgeted up front.  This entry point serves them: it calls no
+// cudaMalloc, cudaFree or other allocating routine.  The scratch is a
+// file-scope __device__ array of kStaticScratchBytes bytes; every GPU that
+// loads the library holds it until the process exits.
+#include <mutex>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+constexpr size_t kStaticScratchBytes = 64ull << 20;   // 64 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device addresses of g_static_scratch, one per device, filled on first use.
+static void *g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mutex;
+
+static cudaError_t static_scratch(int device, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[device] = ptr;
+    }
+    *out = g_scratch_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+extern "C" bf_status bf_execute_nct_static(bf_plan *p, const void *x, int T, float *out, void *stream)
+{
+    if (!p) return set_error(BF_ERR_ARG, "plan is NULL");
+    if (p->layout != BF_LAYOUT_NCT || p->wf.simt)
+        return set_error(BF_ERR_UNSUPPORTED, "bf_execute_nct_static runs antenna-major tensor-core plans");
+    if (T < 0) return set_error(BF_ERR_ARG, "n_samp must be >= 0");
+    if (T / p->t_int == 0) return BF_OK;
+    if (!x || !out) return set_error(BF_ERR_ARG, "NULL voltage or output pointer");
+    if (((uintptr_t)x & 15) || ((uintptr_t)out & 3))
+        return set_error(BF_ERR_ARG, "voltages must be 16-byte aligned and outputs 4-byte aligned");
+    const size_t n_samp = (size_t)p->C * T * p->N;
+    const size_t turned = (n_samp * dtype_sample_bytes(p->dtype) + 255) / 256 * 256;
+    const bool expand = p->dtype == BF_CI8 || p->dtype == BF_CI4;
+    const size_t need = turned + (expand ? n_samp * 4 : 0);
+    if (need > kStaticScratchBytes)
+        return set_error(BF_ERR_ARG, "input needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +
+                                         std::to_string(kStaticScratchBytes) + " (use bf_execute, or fewer samples)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return set_error(BF_ERR_UNSUPPORTED, "device index out of range");
+    void *scr = nullptr;
+    if ((e = static_scratch(dev, &scr)) != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
+    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
+    uint8_t *base = (uint8_t *)scr;
+    e = launch_corner_turn(x, p->dtype, base, p->dtype, p->N, p->C, T, nullptr, s);
+    if (e != cudaSuccess) return cuda_error(e, "corner turn");
+    const void *xin = base;
+    if (expand) {
+        e = launch_expand_to_f16(base, p->dtype, base + turned, (long long)n_samp, p->N, s);
+        if (e != cudaSuccess) return cuda_error(e, "integer expansion");
+        xin = base + turned;
+    }
+    TcArgs ta;
+    ta.x = xin;
+    ta.c_base = 0;
+    ta.c_launch = p->C;
+    ta.c_total = p->C;
+    ta.T = T;
+    ta.T_o = T / p->t_int;
+    ta.t_int = p->t_int;
+    ta.complex_out = 0;
+    ta.out = out;
+    std::string why;
+    e = launch_tc(p, ta, s, &why);
+    if (e != cudaSuccess) {
+        if (!why.empty()) return set_error(BF_ERR_CUDA, "tensor-core kernel: " + why);
+        return cuda_error(e, "tensor-core kernel");
+    }
+    return BF_OK;
+}
