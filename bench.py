@@ -68,8 +68,9 @@ def profiled_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; only the
+    samples taken inside [start, stop] of the timed region are kept."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -77,6 +78,7 @@ class ClockSampler:
         self.gpu = gpu
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -84,10 +86,16 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200", "-f", self.path],
+                 "-i", str(self.gpu), "-lms", "100", "-f", self.path],
                 stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -98,21 +106,26 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         rows = []
+        import datetime
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), float(parts[4]), parts[6:10]))
             except ValueError:
                 continue
         os.unlink(self.path)
-        if not rows:
+        inside = [r for r in rows if self.t0 is not None and self.t0 <= r[0] <= (self.t1 or r[0])]
+        use = inside or rows
+        if not use:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[4]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "power_w_max": max(r[3] for r in use), "samples": len(use),
+                "samples_in_timed_region": len(inside), "reasons": reasons}
 
 
 def dist_env():
@@ -122,13 +135,18 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_oracle_rate(scene, dirs, t_int, n_chan, threads=0):
+def cpu_oracle_rate(scene, dirs, t_int, n_chan, threads=0, x_cache=None):
     """FP64 oracle (plain C, one thread per channel range) on the first
-    ``n_chan`` channels: returns (TFLOP/s, seconds)."""
+    ``n_chan`` channels and the given beams: returns (TFLOP/s, seconds)."""
     import oracle
     chans = list(range(n_chan))
-    x = synth.voltages(scene, synth.C16F, channels=chans)
-    X64 = oracle.decode_voltages(synth.C16F, x)
+    if x_cache is not None and x_cache.get("n") == n_chan:
+        X64 = x_cache["X"]
+    else:
+        x = synth.voltages(scene, synth.C16F, channels=chans)
+        X64 = oracle.decode_voltages(synth.C16F, x)
+        if x_cache is not None:
+            x_cache.update(n=n_chan, X=X64)
     t0 = time.perf_counter()
     W = oracle.weights(scene.pos, scene.freqs[chans], dirs)
     oracle.power(W, X64, t_int, threads=threads)
@@ -137,20 +155,30 @@ def cpu_oracle_rate(scene, dirs, t_int, n_chan, threads=0):
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, each step a bounded sample of the
+    workload (all samples of a channel subset for a beam subset), sized so the
+    whole run takes about two minutes."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     scene, dirs, t_int = synth.config2()
     cores = os.cpu_count() or 1
     n_chan = min(scene.n_chan, cores)
+    cache = {}
+    _, dt_full = cpu_oracle_rate(scene, dirs[:64], t_int, n_chan, x_cache=cache)   # calibration
+    per_beam = dt_full / 64
+    budget = 120.0 / (args.steps + args.warmup)
+    n_beam = int(max(8, min(dirs.shape[0], budget / max(per_beam, 1e-9))))
+    sub = dirs[:n_beam]
     rates = []
     for i in range(args.warmup + args.steps):
-        r, dt = cpu_oracle_rate(scene, dirs, t_int, n_chan)
+        r, dt = cpu_oracle_rate(scene, sub, t_int, n_chan, x_cache=cache)
         if i >= args.warmup:
             rates.append((r, dt))
     value = statistics.mean(r for r, _ in rates)
     ms = 1e3 * statistics.mean(dt for _, dt in rates)
-    sample = f"{n_chan} of 1024 channels, all 1024 beams and 15625 samples per step"
+    sample = (f"{n_chan} of 1024 channels x {n_beam} of 1024 beams x all 15625 samples per step, "
+              f"FP64 oracle, {cores} threads")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -213,7 +241,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
-        time.sleep(0.3)
+        time.sleep(0.5)   # let nvidia-smi start sampling
+        clocks.mark_start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -222,6 +251,7 @@ def run_ours(args):
         step(i, evs[i])
     t_end.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_stop()
     clk = clocks.stop() if rank == 0 else None
     plan.sync()
     total_ms = t_start.elapsed_time(t_end)
@@ -321,8 +351,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true")
