@@ -45,7 +45,8 @@ struct TcRequest {
 // Tensor-core launch configuration.
 struct TcConfig {
     int nt = 256;        // time-tile (MMA N)
-    int xst = 2;         // voltage stages in flight
+    int xst = 2;         // voltage stages in flight (streamed: weight+voltage K-block stages)
+    bool stream = false; // weights streamed per K block instead of resident
     int nsplit = 2;      // epilogue column halves
     int group = 1;       // M tiles whose weights stay resident per work unit
     int n_groups = 1;

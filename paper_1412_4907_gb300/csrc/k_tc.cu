@@ -53,7 +53,7 @@ constexpr int kTcThreads = (3 + kEpiWarps) * 32;
 constexpr int kStageDepth = 4;                     // staged tiles in flight
 constexpr int kTmemCols = 512;
 constexpr int kMaxWinPerTile = 16;
-constexpr int kMaxXStages = 4;
+constexpr int kMaxXStages = 8;
 constexpr int kMaxAcc = 8;                         // TMEM accumulators (512 columns / tile)
 constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
 
@@ -136,7 +136,9 @@ __device__ __forceinline__ float sumsq_pk(const uint32_t *r)
 
 // WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
 // -1 = any T_int (per-column window counter).
-template <bool F8, int WIN, bool COMPLEX>
+// STREAM: weights are not resident; every pipeline stage carries one 64-column
+// K block of the weight tile and of the voltage tile (large antenna counts).
+template <bool F8, int WIN, bool COMPLEX, bool STREAM>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
 {
@@ -201,7 +203,92 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const long long ct1 = a.ct_total * (set + 1) / n_sets;
     const int c_first = (int)(ct0 / a.t_tiles), tt_first = (int)(ct0 % a.t_tiles);
 
-    if (warp == 0) {
+    if (warp == 0 && STREAM) {
+        // ----------------------------------------------- producer, streamed weights
+        if (lane == 0) {
+            uint32_t cnt = 0, issued = 0;
+            int st = 0;
+            bool ok = true;
+            for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+                int m0, gs;
+                group_tiles(a, g, m0, gs);
+                int c = c_first, tt = tt_first;
+                for (long long ct = ct0; ct < ct1 && ok; ++ct) {
+                    for (int s = 0; s < gs && ok; ++s)
+                        for (int kb = 0; kb < a.kb; ++kb) {
+                            if (!mbar_wait(b_xempty + 8 * st, ((cnt >> st) & 1u) ^ 1u, abort_flag, a.err,
+                                           kWaitLimitCycles)) {
+                                ok = false;
+                                break;
+                            }
+                            cnt ^= 1u << st;
+                            issued |= 1u << st;
+                            const uint32_t dst = sx + st * a.x_stage_bytes;
+                            mbar_arrive_expect_tx(b_xfull + 8 * st, a.x_stage_bytes);
+                            tma_load_3d(dst, &wmap, b_xfull + 8 * st, kb * a.ke, (m0 + s) * kRowsPerMTile,
+                                        a.c_base + c);
+                            tma_load_3d(dst + 16384, &xmap, b_xfull + 8 * st, kb * a.ke, tt * a.nt, c);
+                            if (++st == a.xst) st = 0;
+                        }
+                    if (++tt == a.t_tiles) {
+                        tt = 0;
+                        ++c;
+                    }
+                }
+            }
+            if (*abort_flag)
+                for (int i = 0; i < a.xst; ++i)
+                    if (issued & (1u << i)) drain_wait(b_xfull + 8 * i, ((cnt >> i) & 1u) ^ 1u);
+        }
+        __syncwarp();
+    } else if (warp == 1 && STREAM) {
+        // ---------------------------------------------- MMA issuer, streamed weights
+        if (lane == 0) {
+            uint32_t par = 0, tpar = 0;
+            int st = 0, acc = 0;
+            bool ok = true;
+            for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+                int m0, gs;
+                group_tiles(a, g, m0, gs);
+                (void)m0;
+                for (long long ct = ct0; ct < ct1 && ok; ++ct)
+                    for (int s = 0; s < gs && ok; ++s) {
+                        if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err,
+                                       kWaitLimitCycles)) {
+                            ok = false;
+                            break;
+                        }
+                        tpar ^= 1u << acc;
+                        tc_fence_after();
+                        const uint32_t d = tmem + acc * a.nt;
+                        for (int kb = 0; kb < a.kb; ++kb) {
+                            if (!mbar_wait(b_xfull + 8 * st, (par >> st) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                                ok = false;
+                                break;
+                            }
+                            par ^= 1u << st;
+                            tc_fence_after();
+                            const uint32_t base_w = sx + st * a.x_stage_bytes;
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t ad = sdesc_sw128(base_w + ks * 32);
+                                const uint64_t bd = sdesc_sw128(base_w + 16384 + ks * 32);
+                                if (F8) mma_f8(d, ad, bd, a.idesc, (kb | ks) != 0);
+                                else mma_f16(d, ad, bd, a.idesc, (kb | ks) != 0);
+                            }
+                            mma_commit(b_xempty + 8 * st);
+                            if (++st == a.xst) st = 0;
+                        }
+                        if (!ok) break;
+                        mma_commit(b_tfull + 8 * acc);
+                        if (++acc == a.nacc) acc = 0;
+                    }
+            }
+            mma_commit(b_drain);
+            drain_wait(b_drain, 0);
+        }
+        __syncwarp();
+    } else if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t xcnt = 0, wcnt = 0, x_issued = 0, w_issued = 0;
@@ -569,6 +656,32 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
         return false;
     }
     const int mt = f.m_pad / kRowsPerMTile;
+    if (f.kb >= 4) {
+        // many antennas: stream weight and voltage K blocks through a ring of stages
+        for (int nt = 256; nt >= (int)unit; nt -= 16) {
+            if (nt % unit) continue;
+            if (req.tile_t && nt != req.tile_t) continue;
+            if (nt / t_int > kMaxWinPerTile) continue;
+            const int stage = 16384 + nt * 128;
+            const int fixed = stage_bytes() + ctrl_bytes() + 1024;
+            int xst = std::min(kMaxXStages, (kSmemLimit - fixed) / stage);
+            if (req.x_stages) xst = std::min(xst, req.x_stages);
+            if (xst < 2) continue;
+            TcConfig c;
+            c.stream = true;
+            c.nt = nt;
+            c.xst = xst;
+            c.nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
+            c.fast_windows = (t_int % 16) == 0;
+            c.n_groups = 1;
+            c.group = mt;
+            c.smem = std::max(fixed + xst * stage, 116 * 1024);
+            *cfg = c;
+            return true;
+        }
+        *why = "requested tile configuration does not fit the streamed tensor-core kernel";
+        return false;
+    }
     for (int nt = 256; nt >= (int)unit; nt -= 16) {
         if (nt % unit) continue;
         if (req.tile_t && nt != req.tile_t) continue;
@@ -614,11 +727,11 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
     return false;
 }
 
-template <bool F8, int WIN, bool CPX>
+template <bool F8, int WIN, bool CPX, bool STREAM>
 static cudaError_t launch_one(const CUtensorMap &xm, const CUtensorMap &wm, const TcKernelArgs &ka, int grid,
                               int smem, cudaStream_t s)
 {
-    auto kern = k_tc<F8, WIN, CPX>;
+    auto kern = k_tc<F8, WIN, CPX, STREAM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kTcThreads, smem, s>>>(xm, wm, ka);
@@ -688,7 +801,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const uint32_t fmt = (f.op == kOpBF16) ? 1u : 0u;   // F16 = 0, BF16 = 1; E4M3 = 0 for f8f6f4
     ka.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(cfg.nt >> 3) << 17) |
                ((uint32_t)(kRowsPerMTile >> 4) << 24);
-    ka.x_stage_bytes = (uint32_t)(f.kb * cfg.nt * 128);
+    ka.x_stage_bytes = cfg.stream ? (uint32_t)(16384 + cfg.nt * 128) : (uint32_t)(f.kb * cfg.nt * 128);
     ka.w_slot_bytes = (uint32_t)(f.kb * 16384);
     ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
@@ -700,24 +813,27 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const long long n_sets = std::max<long long>(1, std::min<long long>(p->num_sms / ka.gq, ka.ct_total));
     const int grid = (int)(n_sets * ka.gq);
     const bool f8 = f.op == kOpE4M3;
-    if (ta.complex_out) {
-        if (f8) return launch_one<true, 0, true>(xm, wm, ka, grid, cfg.smem, s);
-        return launch_one<false, 0, true>(xm, wm, ka, grid, cfg.smem, s);
-    }
     const int win = (ta.t_int == 64 || ta.t_int == 32 || ta.t_int == 16) ? ta.t_int : (ta.t_int % 16 == 0 ? 0 : -1);
-#define BF_TC_WIN(F8V)                                                         \
-    switch (win) {                                                             \
-    case 64: return launch_one<F8V, 64, false>(xm, wm, ka, grid, cfg.smem, s); \
-    case 32: return launch_one<F8V, 32, false>(xm, wm, ka, grid, cfg.smem, s); \
-    case 16: return launch_one<F8V, 16, false>(xm, wm, ka, grid, cfg.smem, s); \
-    case 0: return launch_one<F8V, 0, false>(xm, wm, ka, grid, cfg.smem, s);   \
-    default: return launch_one<F8V, -1, false>(xm, wm, ka, grid, cfg.smem, s); \
+#define BF_TC_ALL(F8V, STV)                                                                 \
+    if (ta.complex_out) return launch_one<F8V, 0, true, STV>(xm, wm, ka, grid, cfg.smem, s); \
+    switch (win) {                                                                          \
+    case 64: return launch_one<F8V, 64, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
+    case 32: return launch_one<F8V, 32, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
+    case 16: return launch_one<F8V, 16, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
+    case 0: return launch_one<F8V, 0, false, STV>(xm, wm, ka, grid, cfg.smem, s);            \
+    default: return launch_one<F8V, -1, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
+    }
+    if (cfg.stream) {
+        if (f8) {
+            BF_TC_ALL(true, true)
+        }
+        BF_TC_ALL(false, true)
     }
     if (f8) {
-        BF_TC_WIN(true)
+        BF_TC_ALL(true, false)
     }
-    BF_TC_WIN(false)
-#undef BF_TC_WIN
+    BF_TC_ALL(false, false)
+#undef BF_TC_ALL
 }
 
 }  // namespace bfi

@@ -234,7 +234,7 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (mx > 0.f) sig = mx / Q::qmax;
+        if (mx > 0.f) sig = mx / (Q::qmax > 0.f ? Q::qmax : 1.f);
     }
     const float delta = 4e-7f / sig;   // FP32 weight error bound in stored units
 
@@ -287,7 +287,7 @@ __global__ void k_weights_tc(const double *__restrict__ freqs, const double *__r
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const double sig64 = mx > 0.0 ? mx / (double)Q::qmax : 1.0;
+        const double sig64 = mx > 0.0 ? mx / (double)(Q::qmax > 0.f ? Q::qmax : 1.f) : 1.0;
         for (int n = lane; n < n_cols; n += 32) {
             double2 d = weight_at64(ph, mask, b, n, N, B);
             const double re = d.x / sig64, im = d.y / sig64;
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256) k_weights2(const double *__restrict__ fre
                 for (int k = 0; k < nw; ++k) mx = fmaxf(mx, red[w0 + k]);
                 __syncthreads();
             }
-            if (mx > 0.f) sig = mx / Q::qmax;
+            if (mx > 0.f) sig = mx / (Q::qmax > 0.f ? Q::qmax : 1.f);
         }
         // quantise, store, note components within the FP32 error of a boundary
         bool near_any = false;
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256) k_weights2(const double *__restrict__ fre
                     for (int k = 0; k < nw; ++k) mx = fmax(mx, redd[w0 + k]);
                     asm volatile("bar.sync %0, %1;" ::"r"(1 + bl), "r"(g.tpb) : "memory");
                 }
-                const double sig64 = mx > 0.0 ? mx / (double)Q::qmax : 1.0;
+                const double sig64 = mx > 0.0 ? mx / (double)(Q::qmax > 0.f ? Q::qmax : 1.f) : 1.0;
                 if (in_block) {
 #pragma unroll
                     for (int a = 0; a < 2; ++a) {

@@ -204,6 +204,10 @@ def test_tc_modes_ragged(bf, mode):
     (16, 40, 640, 32, synth.C8E4M3),     # FP8 with a padded K block
     (40, 50, 333, 16, synth.CI8),
     (32, 64, 100, 128, synth.C16F),      # T < tile
+    (256, 70, 300, 64, synth.C16BF),     # streamed weights: 8 K blocks
+    (256, 64, 512, 64, synth.C8E4M3),    # streamed, FP8 (4 K blocks of 128 bytes)
+    (512, 65, 256, 64, synth.CI8),       # streamed, 16 K blocks, int8 expanded to FP16
+    (128, 200, 1000, 16, synth.C16F),    # streamed, T_int 16
 ])
 def test_tc_shapes(bf, n_ant, n_beam, n_samp, t_int, mode):
     sigma = 16.0 if mode in (synth.CI8, synth.C8E4M3) else 0.7071
@@ -213,6 +217,24 @@ def test_tc_shapes(bf, n_ant, n_beam, n_samp, t_int, mode):
     P, q = run_power(bf, scene, dirs, t_int, mode, x)
     check(f"tc_N{n_ant}_B{n_beam}_T{n_samp}_Ti{t_int}", P,
           oracle_power_for_mode(scene, dirs, t_int, mode, X64), mode, tile=q["tile_t"])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8])
+def test_config3_shape_precision_modes(bf, mode):
+    """The precision-sweep shape per channel (256 antennas on a 200 m random
+    layout, 2048 beams, 8192 samples, T_int 64, sigma 16 + one 10 dB source)
+    on 2 of its channels: kernel error against the oracle with the same
+    stored values, and the end-to-end error against the FP64 beamformer of the
+    unquantised FP32 base voltages (recorded per mode)."""
+    scene, dirs, t_int = synth.config3(n_chan=2)
+    x, X64 = stored_voltages(scene, mode)
+    P, q = run_power(bf, scene, dirs, t_int, mode, x)
+    check("config3_shape_kernel", P, oracle_power_for_mode(scene, dirs, t_int, mode, X64), mode)
+    x32 = synth.voltages(scene, synth.C32).view(np.complex64).astype(np.complex128)
+    P64 = oracle.power(oracle.weights(scene.pos, scene.freqs, dirs), x32, t_int)
+    mx, l2 = rel_errors(P, P64)
+    record("config3_shape_vs_fp64", mx, l2, mode=synth.MODE_NAMES[mode])
 
 
 @pytest.mark.parametrize("tile", [64, 128, 192, 256])
