@@ -643,8 +643,27 @@ static int gcd_i(int x, int y)
     return x;
 }
 
-static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * 16 + 2 * kStageDepth) + 16; }
 static int stage_bytes() { return kStageDepth * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
+static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * 16 + 2 * kStageDepth) + 16; }
+
+// End of the kernel's shared-memory layout for a configuration, computed the
+// way the kernel computes its offsets (1024 bytes of alignment slack, voltage
+// or K-block stages, resident weight slots, staging ring, barriers, TMEM
+// holder and abort flag).
+static size_t layout_end(const TcConfig &c, int kb)
+{
+    const size_t x_stage = c.stream ? (size_t)(16384 + c.nt * 128) : (size_t)kb * c.nt * 128;
+    const size_t gmax = c.stream ? 0 : (size_t)c.group;
+    const size_t w_slot = c.stream ? 0 : (size_t)kb * 16384;
+    return 1024 + (size_t)c.xst * x_stage + gmax * w_slot + (size_t)stage_bytes() +
+           8 * (size_t)(2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * gmax + 2 * kStageDepth) + 8;
+}
+
+static bool layout_ok(const TcConfig &c, int kb)
+{
+    return layout_end(c, kb) <= (size_t)c.smem && c.smem <= kSmemLimit && c.xst >= 2 && c.xst <= kMaxXStages &&
+           (c.stream || c.group <= 16) && c.nt >= 16 && c.nt <= 256 && c.nt % 16 == 0;
+}
 
 bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why)
 {
@@ -676,6 +695,10 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
             c.n_groups = 1;
             c.group = mt;
             c.smem = std::max(fixed + xst * stage, 116 * 1024);
+            if (!layout_ok(c, f.kb)) {
+                *why = "internal tiling inconsistency (shared-memory layout exceeds the allocation)";
+                return false;
+            }
             *cfg = c;
             return true;
         }
@@ -718,6 +741,10 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
             }
         }
         if (!found) continue;
+        if (!layout_ok(best, f.kb)) {
+            *why = "internal tiling inconsistency (shared-memory layout exceeds the allocation)";
+            return false;
+        }
         *cfg = best;
         return true;
     }
@@ -781,7 +808,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.n_groups = cfg.n_groups;
     ka.g_base = mt / cfg.n_groups;
     ka.g_rem = mt % cfg.n_groups;
-    ka.gmax = cfg.group;
+    ka.gmax = cfg.stream ? 0 : cfg.group;   // streamed weights have no resident slots
     ka.t_tiles = (ta.T + cfg.nt - 1) / cfg.nt;
     ka.ct_total = (long long)ta.c_launch * ka.t_tiles;
     ka.nt = cfg.nt;
@@ -802,12 +829,16 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(cfg.nt >> 3) << 17) |
                ((uint32_t)(kRowsPerMTile >> 4) << 24);
     ka.x_stage_bytes = cfg.stream ? (uint32_t)(16384 + cfg.nt * 128) : (uint32_t)(f.kb * cfg.nt * 128);
-    ka.w_slot_bytes = (uint32_t)(f.kb * 16384);
+    ka.w_slot_bytes = cfg.stream ? 0u : (uint32_t)(f.kb * 16384);
     ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
     ka.err = p->d_err;
     if (ka.ct_total == 0) return cudaSuccess;
+    if (!layout_ok(cfg, f.kb) || ka.gmax != (cfg.stream ? 0 : cfg.group)) {   // final guard before launch
+        *why = "internal tiling inconsistency (shared-memory layout exceeds the allocation)";
+        return cudaErrorInvalidConfiguration;
+    }
     // sets of gq CTAs hold different weight groups and walk the same range in step
     ka.gq = std::min(cfg.n_groups, p->num_sms);
     const long long n_sets = std::max<long long>(1, std::min<long long>(p->num_sms / ka.gq, ka.ct_total));

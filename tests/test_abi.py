@@ -107,3 +107,22 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     (pkg / "__init__.py").write_text(src)
     r = subprocess.run(["python", "-c", code], capture_output=True, text=True)
     assert r.returncode != 0 and "not built" in r.stderr
+
+
+def test_planner_layouts_fit_shared_memory(bf):
+    """Every tiling the planner picks keeps the kernel's shared-memory layout
+    inside the allocation (checked on the host before any CUDA call)."""
+    import itertools
+    for n_ant, n_beam, dtype, t_int in itertools.product(
+            (4, 8, 16, 32, 40, 64, 96, 128, 192, 256, 384, 512), (1, 65, 1024, 4096),
+            (bf.BF_C16F, bf.BF_C16BF, bf.BF_C8E4M3, bf.BF_CI8, bf.BF_CI4), (1, 10, 16, 48, 64, 128, 256)):
+        if dtype == bf.BF_C8E4M3 and n_ant % 8:
+            continue
+        pos = np.zeros((n_ant, 3))
+        dirs = np.tile([0.0, 0.0, 1.0], (n_beam, 1))
+        try:
+            h = bf.bf_plan_create(pos, np.array([4e8]), dirs, dtype, t_int)
+            bf.bf_destroy(h)          # a GPU is present: the plan was built
+        except bf.BFError as e:
+            assert "inconsistency" not in str(e), (n_ant, n_beam, dtype, t_int, str(e))
+            assert e.status in (bf.BF_ERR_CUDA, bf.BF_ERR_UNSUPPORTED, bf.BF_ERR_NOMEM), str(e)
