@@ -41,6 +41,15 @@ def flops(n_ant, n_beam, n_chan, n_samp):
     return 8.0 * n_ant * n_beam * n_chan * n_samp
 
 
+def power_errors(P, P_ref):
+    """(max relative error with a floor of 1e-3 x mean, L2 relative error)."""
+    P = np.asarray(P, dtype=np.float64)
+    P_ref = np.asarray(P_ref, dtype=np.float64)
+    floor = 1e-3 * max(P_ref.mean(), 1e-300)
+    return (float(np.max(np.abs(P - P_ref) / np.maximum(P_ref, floor))),
+            float(np.linalg.norm(P - P_ref) / max(np.linalg.norm(P_ref), 1e-300)))
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -348,6 +357,75 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Precision sweep on the config-3 shape (256 antennas on a 200 m random
+    layout, 2048 beams, 8192 samples, T_int 64) over the first ``--channels``
+    channels (default 256): per mode, fused-kernel TFLOP/s and roofline
+    fraction, and the power error on two sampled channels against the FP64
+    oracle fed the same stored values (kernel error) and fed the unquantised
+    FP32 base voltages (end to end).  One JSON line per mode."""
+    import torch
+
+    import oracle
+    import paper_1412_4907_gb300 as bf
+    torch.cuda.set_device(0)
+    n_chan = args.channels or 256
+    scene, dirs, t_int = synth.config3(n_chan=n_chan)
+    N, B, T = scene.n_ant, dirs.shape[0], scene.n_samp
+    F = flops(N, B, n_chan, T)
+    pk, pk_kind = peaks()
+    bf16_peak = pk["bf16_tflops_sustained"]
+    # tensor peak per operand type: FP8 runs at twice the 16-bit rate; int8 and
+    # 4-bit inputs are multiplied as FP16; FP32 runs on the CUDA cores
+    peak = {synth.C16F: bf16_peak, synth.C16BF: bf16_peak, synth.C8E4M3: 2 * bf16_peak,
+            synth.CI8: bf16_peak}
+    chans = [3, n_chan - 5]
+    x32_sub = synth.voltages(scene, synth.C32, channels=chans).view(np.complex64).astype(np.complex128)
+    sub_freqs = scene.freqs[chans]
+    W64 = oracle.weights(scene.pos, sub_freqs, dirs)
+    P64 = oracle.power(W64, x32_sub, t_int)
+    stream = torch.cuda.current_stream()
+    for mode in (synth.C32, synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8):
+        x = synth.voltages(scene, mode)
+        xd = torch.from_numpy(x).cuda()
+        del x
+        plan = bf.Plan(scene.pos, scene.freqs, dirs, mode, t_int, stream=stream)
+        out = torch.empty((B, n_chan, T // t_int), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            plan.execute(xd, out)
+        torch.cuda.synchronize()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(3, min(args.steps, 20))
+        a.record(stream)
+        for _ in range(n):
+            plan.execute(xd, out)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b_) / n
+        plan.sync()
+        P = out[:, chans, :].cpu().numpy()
+        xs = synth.voltages(scene, mode, channels=chans)
+        Wq = W64 if mode == synth.C32 else oracle.quantised_weights(W64, mode)[0]
+        Pq = oracle.power(Wq, oracle.decode_voltages(mode, xs), t_int)
+        kmx, kl2 = power_errors(P, Pq)
+        emx, el2 = power_errors(P, P64)
+        q = plan.query_tiles()
+        plan.close()
+        del xd, out
+        tf = F / (ms * 1e-3) / 1e12
+        line = {"metric": "precision sweep: fused beamform TFLOP/s and power error vs FP64", "mode": synth.MODE_NAMES[mode],
+                "value": tf, "unit": UNIT, "ms_per_launch": ms,
+                "roofline": None if mode == synth.C32 else {"bound": "tensor", "achieved": tf, "peak": peak[mode],
+                                                            "frac": tf / peak[mode], "unit": "TFLOP/s",
+                                                            "peak_source": f"bf16_tflops_sustained {pk_kind}"
+                                                                           + (" x 2 (FP8 nominal ratio)" if mode == synth.C8E4M3 else "")},
+                "error_kernel": {"max_rel": kmx, "l2_rel": kl2},
+                "error_vs_fp64": {"max_rel": emx, "l2_rel": el2, "channels": chans},
+                "tiling": q, "config": {"workload": f"config-3 shape: 256 antennas, 2048 beams, 8192 samples, T_int 64, "
+                                                    f"{n_chan} of 4096 channels", "input_sigma": 16.0}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,12 +435,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep on the config-3 shape (one JSON line per mode) instead of the benchmark")
     ap.add_argument("--channels", type=int, default=0,
                     help="run only the first C channels (same per-channel shape; for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 
