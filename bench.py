@@ -60,7 +60,7 @@ def peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("k_tc.cu", "ptx.cuh", "bf_internal.h"):
+    for f in ("k_tc.cu", "tc_common.cuh", "ptx.cuh", "bf_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1412_4907_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -246,6 +246,79 @@ bf_status bf_corner_turn(const void *d_in, int in_dtype, void *d_out, int out_dt
                          void *stream);
 
 /*
+ * Batched execution: the jobs of several plans in ONE persistent launch.
+ *
+ * A batch groups plans that differ in antennas, beams, channels and sample
+ * counts (sub-arrays, beam sets, observing modes sharing a GPU) so that a
+ * step over all of them is a single kernel launch whose CTAs split the work
+ * by cost (MMA K blocks per tile), instead of one under-filled launch per
+ * plan.  Section 4 measures one beamformer configuration at a time; this is
+ * the same computation (Eq. 1 weights, Section 2.1 fused power detection)
+ * applied to many configurations at once.
+ *
+ * Every plan of a batch must be a tensor-core plan (not BF_C32) in the CTN
+ * layout, on one device, with the same operand format (BF_C16F, BF_CI8 and
+ * BF_CI4 share the FP16 format; BF_C16BF and BF_C8E4M3 stand alone) and the
+ * same T_int.  The batch keeps pointers to the plans: they must outlive it,
+ * and their weights are read at execution time (bf_weights on a member plan
+ * takes effect at the next batch step, stream-ordered as usual).
+ */
+typedef struct bf_batch bf_batch;
+
+/*
+ * bf_batch_create — batch over plans[0 .. n_plans-1] (host array, read
+ * during the call).  tile_t = 0 chooses the widest tile (samples per MMA, a
+ * multiple of 16 and of T_int, at most 256 and 16 windows); otherwise that
+ * width.  Allocates the device job table (one 256-byte entry per plan) and a
+ * pinned host copy.  Errors: BF_ERR_ARG (NULL or empty), BF_ERR_UNSUPPORTED
+ * (plans that cannot share a launch, no tile width fits), BF_ERR_NOMEM /
+ * BF_ERR_CUDA.
+ */
+bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, int tile_t);
+
+/*
+ * bf_batch_set — bind job `job` (index into the plans given at creation) to
+ *  d_voltages  device, CTN [C][n_samp][N] complex samples of the plan's dtype,
+ *              16-byte aligned (N * sample bytes a multiple of 16 for TMA);
+ *  n_samp      samples per channel (0 = the job contributes nothing);
+ *  d_power     device, float [B][C][n_samp / T_int], 16-byte aligned.
+ * Waits for the batch's last step to finish (the job table it read is
+ * rewritten) and discards a captured graph.  Errors: BF_ERR_ARG.
+ */
+bf_status bf_batch_set(bf_batch *batch, int job, const void *d_voltages, int n_samp, float *d_power);
+
+/*
+ * bf_batch_execute — one step over every job on `stream` (NULL = the legacy
+ * default stream): integer inputs are widened to FP16 in batch-owned
+ * buffers, the job table is copied up, and one persistent launch computes
+ * all powers.  Asynchronous.  Errors: BF_ERR_STATE if a job was never set.
+ */
+bf_status bf_batch_execute(bf_batch *batch, void *stream);
+
+/*
+ * bf_batch_capture / bf_batch_replay — record one bf_batch_execute on
+ * `stream` (non-NULL, not already capturing) into a CUDA graph, then launch
+ * that graph on any stream.  Replays read the inputs and write the outputs
+ * bound by bf_batch_set at capture time; a later bf_batch_set drops the
+ * graph (BF_ERR_STATE from replay until captured again).
+ */
+bf_status bf_batch_capture(bf_batch *batch, void *stream);
+bf_status bf_batch_replay(bf_batch *batch, void *stream);
+
+/* bf_batch_sync — wait for the batch's last step; BF_ERR_TIMEOUT if a
+ * device-side wait of that step gave up (the flag is then cleared). */
+bf_status bf_batch_sync(bf_batch *batch);
+
+/* bf_batch_query — tile width, work units (channel x time tile x 64-beam
+ * block over all jobs) and useful FLOPs per step (8 N B C n_samp summed over
+ * jobs); any output may be NULL. */
+bf_status bf_batch_query(const bf_batch *batch, int *tile_t, long long *units, double *flops);
+
+/* bf_batch_destroy — wait for the last step and free the batch (not the
+ * plans).  NULL is a no-op. */
+bf_status bf_batch_destroy(bf_batch *batch);
+
+/*
  * bf_execute_nct_static — bf_execute for an antenna-major (BF_LAYOUT_NCT)
  * tensor-core plan that allocates nothing.  The paper has no counterpart: it
  * exists for callers that cannot allocate device memory when they execute

@@ -48,6 +48,14 @@ SIGNATURES = {
     "bf_plan_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_S)],
     "bf_export_weights": [_P, _P, _P],
     "bf_corner_turn": [_P, _I, _P, _I, _I, _I, _I, _P, _P],
+    "bf_batch_create": [ctypes.POINTER(_P), _P, _I, _I],
+    "bf_batch_set": [_P, _I, _P, _I, _P],
+    "bf_batch_execute": [_P, _P],
+    "bf_batch_capture": [_P, _P],
+    "bf_batch_replay": [_P, _P],
+    "bf_batch_sync": [_P],
+    "bf_batch_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
+    "bf_batch_destroy": [_P],
     "bf_execute_nct_static": [_P, _P, _I, _P, _P],
 }
 
@@ -171,6 +179,43 @@ def bf_corner_turn(d_in: int, in_dtype: int, d_out: int, out_dtype: int, n_ant: 
                                stream or None))
 
 
+def bf_batch_create(plans, tile_t: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    b = ctypes.c_void_p()
+    _check(_lib.bf_batch_create(ctypes.byref(b), arr, len(plans), tile_t))
+    return b.value
+
+
+def bf_batch_set(batch: int, job: int, d_voltages: int, n_samp: int, d_power: int):
+    _check(_lib.bf_batch_set(batch, job, d_voltages or None, n_samp, d_power or None))
+
+
+def bf_batch_execute(batch: int, stream: int = 0):
+    _check(_lib.bf_batch_execute(batch, stream or None))
+
+
+def bf_batch_capture(batch: int, stream: int):
+    _check(_lib.bf_batch_capture(batch, stream or None))
+
+
+def bf_batch_replay(batch: int, stream: int = 0):
+    _check(_lib.bf_batch_replay(batch, stream or None))
+
+
+def bf_batch_sync(batch: int):
+    _check(_lib.bf_batch_sync(batch))
+
+
+def bf_batch_query(batch: int) -> dict:
+    t, u, f = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_double()
+    _check(_lib.bf_batch_query(batch, ctypes.byref(t), ctypes.byref(u), ctypes.byref(f)))
+    return {"tile_t": t.value, "units": u.value, "flops": f.value}
+
+
+def bf_batch_destroy(batch: int):
+    _check(_lib.bf_batch_destroy(batch))
+
+
 # ------------------------------------------------------------ torch helper
 class Plan:
     """A beamforming plan on the current CUDA device.  Voltages are torch
@@ -267,3 +312,53 @@ class Plan:
 
     def sync(self):
         bf_sync(self.handle)
+
+
+class Batch:
+    """Several plans stepped by one persistent launch (``bf_batch_*``).
+    ``set(j, x, out)`` binds job j's voltages and powers (torch tensors);
+    ``execute()`` runs one step on the stream given here; ``capture()`` /
+    ``replay()`` record and relaunch that step as a CUDA graph."""
+
+    def __init__(self, plans, tile_t: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.plans = list(plans)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = bf_batch_create([p.handle for p in self.plans], tile_t)
+        self._bound = [None] * len(self.plans)
+
+    def set(self, job: int, x, out=None, n_samp=None):
+        p = self.plans[job]
+        T = p.n_samp(x) if n_samp is None else n_samp
+        if out is None:
+            out = self._torch.empty((p.B, p.C, T // p.t_int), dtype=self._torch.float32, device=x.device)
+        bf_batch_set(self.handle, job, x.data_ptr(), T, out.data_ptr())
+        self._bound[job] = (x, out)   # keeps the bound tensors alive
+        return out
+
+    def execute(self):
+        bf_batch_execute(self.handle, self.stream.cuda_stream)
+
+    def capture(self):
+        bf_batch_capture(self.handle, self.stream.cuda_stream)
+
+    def replay(self):
+        bf_batch_replay(self.handle, self.stream.cuda_stream)
+
+    def sync(self):
+        bf_batch_sync(self.handle)
+
+    def query(self) -> dict:
+        return bf_batch_query(self.handle)
+
+    def close(self):
+        if self.handle:
+            bf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,663 @@
+// Batched persistent tensor-core beamformer: the jobs of several plans
+// (sub-arrays, beam sets and channel counts of uneven sizes) in one launch.
+//
+// Every job keeps its own plan (weights, per-beam scales) and its own input
+// and output buffers; the batch holds a device table with one entry per job
+// (the two TMA tensor maps and the job's shape).  Work units are
+// (job, channel, time tile, M tile), M tile fastest so a voltage tile is
+// reused from L2 by consecutive MMAs; units are split among the persistent
+// CTAs by cost (K blocks per unit plus one for the epilogue), so jobs of very
+// different antenna counts balance.  Every job runs the streamed-weight
+// pipeline (one 64-column K block of weights and voltages per stage), so any
+// antenna count fits the same kernel; the epilogue and store warp are the
+// single-plan kernel's.  One launch per batch step; it can be captured in a
+// CUDA graph and replayed.
+#include <algorithm>
+#include <mutex>
+
+#include "tc_common.cuh"
+
+namespace bfi {
+
+struct __align__(128) BatchJob {
+    CUtensorMap xmap;   // voltages [C][T][2N]
+    CUtensorMap wmap;   // weight rows [C][M_pad][K_pad]
+    long long unit0;    // first global unit of the job
+    long long units;    // C x t_tiles x mt
+    long long cost0;    // total cost of the jobs before this one
+    int C, t_tiles, mt, kb, ke, w;   // w: cost of one unit
+    int T, T_o, B, b_pad;
+    uint32_t idesc;
+    const float *wscale;   // NULL for unscaled formats
+    const float *wsig;
+    float *out;
+};
+
+struct BatchArgs {
+    const BatchJob *jobs;
+    int n_jobs;
+    long long total_cost;
+    int nt, nsplit, wpt, t_int, xst, nacc;
+    uint32_t stage_bytes;   // 16384 + nt * 128
+    unsigned *err;
+};
+
+// First unit whose cost interval starts at or after `pos`.
+__device__ __forceinline__ long long unit_at(const BatchArgs &a, long long pos)
+{
+    int lo = 0, hi = a.n_jobs - 1;
+    while (lo < hi) {   // last job with cost0 <= pos
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jobs[mid].cost0 <= pos) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchJob &J = a.jobs[lo];
+    const long long k = (pos - J.cost0 + J.w - 1) / J.w;
+    return J.unit0 + min(k, J.units);
+}
+
+__device__ __forceinline__ int job_of(const BatchArgs &a, long long u)
+{
+    int lo = 0, hi = a.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jobs[mid].unit0 <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct UnitPos {
+    int j, c, tt, m;
+};
+
+// Walks this CTA's units in order, tracking the job and decoding positions.
+struct UnitWalk {
+    const BatchArgs *a;
+    long long u, u1;
+    int j;
+    __device__ void begin(const BatchArgs &args, long long u0_, long long u1_)
+    {
+        a = &args;
+        u = u0_;
+        u1 = u1_;
+        j = u < u1 ? job_of(args, u) : 0;
+    }
+    __device__ bool next(UnitPos &p)
+    {
+        if (u >= u1) return false;
+        while (u >= a->jobs[j].unit0 + a->jobs[j].units) ++j;
+        const BatchJob &J = a->jobs[j];
+        const int v = (int)(u - J.unit0);
+        p.j = j;
+        p.m = v % J.mt;
+        const int r = v / J.mt;
+        p.tt = r % J.t_tiles;
+        p.c = r / J.t_tiles;
+        ++u;
+        return true;
+    }
+};
+
+template <bool F8, int WIN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    const uint32_t sx = base;
+    float *stage = reinterpret_cast<float *>(gbase + a.xst * a.stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
+    const uint32_t b_full = smem_u32(bars + 0);                  // [kMaxXStages]
+    const uint32_t b_empty = smem_u32(bars + kMaxXStages);       // [kMaxXStages]
+    const uint32_t b_tfull = smem_u32(bars + 2 * kMaxXStages);   // [kMaxAcc]
+    const uint32_t b_tempty = b_tfull + 8 * kMaxAcc;              // [kMaxAcc]
+    const uint32_t b_drain = b_tempty + 8 * kMaxAcc;
+    const uint32_t b_sfull = b_drain + 8;                         // [kStageDepth]
+    const uint32_t b_sempty = b_sfull + 8 * kStageDepth;          // [kStageDepth]
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < a.xst; ++i) {
+            mbar_init(b_full + 8 * i, 1);
+            mbar_init(b_empty + 8 * i, 1);
+        }
+        for (int i = 0; i < a.nacc; ++i) {
+            mbar_init(b_tfull + 8 * i, 1);
+            mbar_init(b_tempty + 8 * i, kEpiWarps);
+        }
+        mbar_init(b_drain, 1);
+        for (int i = 0; i < kStageDepth; ++i) {
+            mbar_init(b_sfull + 8 * i, 4 * a.nsplit);
+            mbar_init(b_sempty + 8 * i, 1);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    const long long u0 = unit_at(a, a.total_cost * blockIdx.x / gridDim.x);
+    const long long u1 = unit_at(a, a.total_cost * (blockIdx.x + 1) / gridDim.x);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t cnt = 0, issued = 0;
+            int st = 0, pj = -1;
+            UnitWalk w;
+            w.begin(a, u0, u1);
+            UnitPos p;
+            bool ok = true;
+            while (ok && w.next(p)) {
+                const BatchJob &J = a.jobs[p.j];
+                if (p.j != pj) {
+                    prefetch_tensormap(&J.xmap);
+                    prefetch_tensormap(&J.wmap);
+                    pj = p.j;
+                }
+                const uint32_t bytes = 16384 + a.nt * 128;
+                for (int kb = 0; kb < J.kb; ++kb) {
+                    if (!mbar_wait(b_empty + 8 * st, ((cnt >> st) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                        ok = false;
+                        break;
+                    }
+                    cnt ^= 1u << st;
+                    issued |= 1u << st;
+                    const uint32_t dst = sx + st * a.stage_bytes;
+                    mbar_arrive_expect_tx(b_full + 8 * st, bytes);
+                    tma_load_3d(dst, &J.wmap, b_full + 8 * st, kb * J.ke, p.m * kRowsPerMTile, p.c);
+                    tma_load_3d(dst + 16384, &J.xmap, b_full + 8 * st, kb * J.ke, p.tt * a.nt, p.c);
+                    if (++st == a.xst) st = 0;
+                }
+            }
+            if (*abort_flag)
+                for (int i = 0; i < a.xst; ++i)
+                    if (issued & (1u << i)) drain_wait(b_full + 8 * i, ((cnt >> i) & 1u) ^ 1u);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ----------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t par = 0, tpar = 0;
+            int st = 0, acc = 0;
+            UnitWalk w;
+            w.begin(a, u0, u1);
+            UnitPos p;
+            bool ok = true;
+            while (ok && w.next(p)) {
+                const BatchJob &J = a.jobs[p.j];
+                if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                    ok = false;
+                    break;
+                }
+                tpar ^= 1u << acc;
+                tc_fence_after();
+                const uint32_t d = tmem + acc * a.nt;
+                for (int kb = 0; kb < J.kb; ++kb) {
+                    if (!mbar_wait(b_full + 8 * st, (par >> st) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                        ok = false;
+                        break;
+                    }
+                    par ^= 1u << st;
+                    tc_fence_after();
+                    const uint32_t sw = sx + st * a.stage_bytes;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t ad = sdesc_sw128(sw + ks * 32);
+                        const uint64_t bd = sdesc_sw128(sw + 16384 + ks * 32);
+                        if (F8) mma_f8(d, ad, bd, J.idesc, (kb | ks) != 0);
+                        else mma_f16(d, ad, bd, J.idesc, (kb | ks) != 0);
+                    }
+                    mma_commit(b_empty + 8 * st);
+                    if (++st == a.xst) st = 0;
+                }
+                if (!ok) break;
+                mma_commit(b_tfull + 8 * acc);
+                if (++acc == a.nacc) acc = 0;
+            }
+            mma_commit(b_drain);
+            drain_wait(b_drain, 0);
+        }
+        __syncwarp();
+    } else if (warp < kStoreWarp) {
+        // -------------------------------------------------------------- epilogue
+        const int e = warp - 2;
+        const int q = warp & 3;
+        const int h = e >> 2;
+        const int bq = q * 16 + (lane & 15);
+        const int cols = a.nt / a.nsplit;
+        const int col0 = h * cols;
+        const bool active = h < a.nsplit;
+        uint32_t tpar = 0, kt = 0;
+        int acc = 0;
+        UnitWalk w;
+        w.begin(a, u0, u1);
+        UnitPos p;
+        while (w.next(p)) {
+            const BatchJob &J = a.jobs[p.j];
+            if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+            tpar ^= 1u << acc;
+            const uint32_t sb = kt % kStageDepth;
+            if (active && !mbar_wait(b_sempty + 8 * sb, ((kt / kStageDepth) & 1u) ^ 1u, abort_flag, a.err,
+                                     kWaitLimitCycles))
+                break;
+            tc_fence_after();
+            const int b = p.m * kBeamsPerMTile + bq;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
+            const uint32_t tempty = b_tempty + 8 * acc;
+            if (!active) {
+                tile_release(tempty, lane);
+            } else {
+                const TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, J.T, J.T_o, J.B, J.b_pad, J.C, J.wscale, J.wsig, J.out};
+                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < J.B, p.c,
+                                    stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
+            }
+            ++kt;
+            if (++acc == a.nacc) acc = 0;
+        }
+    } else if (warp == kStoreWarp) {
+        // ------------------------------------------------------------ store warp
+        uint32_t kt = 0;
+        UnitWalk w;
+        w.begin(a, u0, u1);
+        UnitPos p;
+        while (w.next(p)) {
+            const BatchJob &J = a.jobs[p.j];
+            const uint32_t sb = kt % kStageDepth;
+            if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+            const TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, J.T, J.T_o, J.B, J.b_pad, J.C, J.wscale, J.wsig, J.out};
+            store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), p.m * kBeamsPerMTile, p.c, p.tt, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
+            ++kt;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+}  // namespace bfi
+
+// ----------------------------------------------------------------- host side
+using namespace bfi;
+
+struct bf_batch {
+    std::vector<bf_plan *> plans;
+    int n = 0;
+    int nt = 256, nsplit = 2, wpt = 4, t_int = 64, xst = 2, nacc = 2, smem = 0;
+    bool f8 = false;
+    int device = 0, num_sms = 0;
+    BatchJob *h_jobs = nullptr;   // pinned, so a captured copy reads it at replay
+    BatchJob *d_jobs = nullptr;
+    std::vector<void *> expand_buf;   // per job, FP16 copies of 8/4-bit inputs
+    std::vector<size_t> expand_bytes;
+    std::vector<const void *> in;
+    std::vector<int> n_samp;
+    std::vector<float *> out;
+    std::vector<char> set;
+    long long total_cost = 0, total_units = 0;
+    double flops = 0.0;
+    cudaStream_t last_stream = nullptr;
+    bool launched = false;   // a step was enqueued on last_stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned *d_err = nullptr;
+};
+
+static int batch_stage_bytes(int nt) { return 16384 + nt * 128; }
+static int batch_layout_end(int xst, int nt)
+{
+    return 1024 + xst * batch_stage_bytes(nt) + kStageDepth * kBeamsPerMTile * kMaxWinPerTile * 4 +
+           8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth) + 8;
+}
+
+static void batch_free(bf_batch *b)
+{
+    if (!b) return;
+    if (b->launched) cudaStreamSynchronize(b->last_stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_err) cudaFree(b->d_err);
+    for (void *p : b->expand_buf)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+// The attribute is a per-kernel maximum shared by every batch: it is set to
+// the largest size any batch asks for, so one batch never lowers another's.
+template <bool F8, int WIN>
+static cudaError_t batch_attr()
+{
+    return cudaFuncSetAttribute(k_tc_batch<F8, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+}
+
+template <bool F8, int WIN>
+static cudaError_t batch_launch(const BatchArgs &ka, int grid, int smem, cudaStream_t s)
+{
+    k_tc_batch<F8, WIN><<<grid, kTcThreads, smem, s>>>(ka);
+    return cudaGetLastError();
+}
+
+static int batch_win(int t_int)
+{
+    return (t_int == 64 || t_int == 32 || t_int == 16) ? t_int : (t_int % 16 == 0 ? 0 : -1);
+}
+
+#define BF_BATCH_DISPATCH(CALL)                                  \
+    do {                                                         \
+        const int win_ = batch_win(b->t_int);                    \
+        if (b->f8) {                                             \
+            switch (win_) {                                      \
+            case 64: e = CALL(true, 64); break;                  \
+            case 32: e = CALL(true, 32); break;                  \
+            case 16: e = CALL(true, 16); break;                  \
+            case 0: e = CALL(true, 0); break;                    \
+            default: e = CALL(true, -1); break;                  \
+            }                                                    \
+        } else {                                                 \
+            switch (win_) {                                      \
+            case 64: e = CALL(false, 64); break;                 \
+            case 32: e = CALL(false, 32); break;                 \
+            case 16: e = CALL(false, 16); break;                 \
+            case 0: e = CALL(false, 0); break;                   \
+            default: e = CALL(false, -1); break;                 \
+            }                                                    \
+        }                                                        \
+    } while (0)
+
+#define BF_ATTR(F, W) batch_attr<F, W>()
+#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, grid, b->smem, s)
+
+static void batch_reindex(bf_batch *b)
+{
+    long long unit0 = 0, cost0 = 0;
+    double fl = 0.0;
+    for (int j = 0; j < b->n; ++j) {
+        BatchJob &J = b->h_jobs[j];
+        J.unit0 = unit0;
+        J.cost0 = cost0;
+        unit0 += J.units;
+        cost0 += J.units * J.w;
+        if (b->set[j]) {
+            const bf_plan *p = b->plans[j];
+            fl += 8.0 * p->N * p->B * p->C * (double)b->n_samp[j];
+        }
+    }
+    b->total_units = unit0;
+    b->total_cost = cost0;
+    b->flops = fl;
+}
+
+extern "C" {
+
+bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, int tile_t)
+{
+    if (!out) return set_error(BF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!plans || n_plans < 1) return set_error(BF_ERR_ARG, "need at least one plan");
+    const bf_plan *p0 = plans[0];
+    if (!p0) return set_error(BF_ERR_ARG, "NULL plan");
+    for (int i = 0; i < n_plans; ++i) {
+        const bf_plan *p = plans[i];
+        if (!p) return set_error(BF_ERR_ARG, "NULL plan");
+        if (p->wf.simt) return set_error(BF_ERR_UNSUPPORTED, "batches run tensor-core plans (not BF_C32)");
+        if (p->layout != BF_LAYOUT_CTN) return set_error(BF_ERR_UNSUPPORTED, "batches take the CTN layout");
+        if (p->wf.op != p0->wf.op && (p->wf.op == kOpE4M3 || p0->wf.op == kOpE4M3))
+            return set_error(BF_ERR_UNSUPPORTED, "FP8 and 16-bit plans cannot share a batch");
+        if (p->wf.op != p0->wf.op)
+            return set_error(BF_ERR_UNSUPPORTED, "all plans of a batch must share the operand format");
+        if (p->t_int != p0->t_int) return set_error(BF_ERR_UNSUPPORTED, "all plans of a batch must share T_int");
+        if (p->device != p0->device) return set_error(BF_ERR_UNSUPPORTED, "all plans must be on one device");
+    }
+    const int t_int = p0->t_int;
+    int g = 16, t = t_int;
+    while (t) {
+        const int r = g % t;
+        g = t;
+        t = r;
+    }
+    const int unit = 16 / g * t_int;   // lcm(16, T_int)
+    int nt = 0;
+    for (int cand = 256; cand >= unit && cand >= 16; cand -= 16) {
+        if (cand % unit || cand / t_int > kMaxWinPerTile) continue;
+        if (tile_t && cand != tile_t) continue;
+        nt = cand;
+        break;
+    }
+    if (!nt) return set_error(BF_ERR_UNSUPPORTED, "no tile width fits this T_int (and request)");
+    bf_batch *b = new bf_batch();
+    b->plans.assign(plans, plans + n_plans);
+    b->n = n_plans;
+    b->nt = nt;
+    b->t_int = t_int;
+    b->nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
+    b->wpt = nt / t_int;
+    b->nacc = std::min(kMaxAcc, kTmemCols / nt);
+    b->f8 = p0->wf.op == kOpE4M3;
+    b->device = p0->device;
+    b->num_sms = p0->num_sms;
+    const int fixed = batch_layout_end(0, nt);
+    b->xst = std::min(kMaxXStages, (kSmemLimit - fixed) / batch_stage_bytes(nt));
+    b->smem = std::max(batch_layout_end(b->xst, nt), 116 * 1024);
+    if (b->xst < 2 || batch_layout_end(b->xst, nt) > b->smem || b->smem > kSmemLimit) {
+        batch_free(b);
+        return set_error(BF_ERR_UNSUPPORTED, "batch stages do not fit in shared memory");
+    }
+    cudaError_t e;
+    if ((e = cudaHostAlloc((void **)&b->h_jobs, sizeof(BatchJob) * n_plans, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_jobs, sizeof(BatchJob) * n_plans)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_err, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(b->d_err, 0, sizeof(unsigned))) != cudaSuccess) {
+        batch_free(b);
+        return cuda_error(e, "batch allocation");
+    }
+    memset((void *)b->h_jobs, 0, sizeof(BatchJob) * n_plans);
+    for (int j = 0; j < n_plans; ++j) b->h_jobs[j].w = 1;
+    b->expand_buf.assign(n_plans, nullptr);
+    b->expand_bytes.assign(n_plans, 0);
+    b->in.assign(n_plans, nullptr);
+    b->n_samp.assign(n_plans, 0);
+    b->out.assign(n_plans, nullptr);
+    b->set.assign(n_plans, 0);
+    BF_BATCH_DISPATCH(BF_ATTR);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_error(e, "batch kernel attribute");
+    }
+    *out = b;
+    return BF_OK;
+}
+
+bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
+{
+    if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
+    if (job < 0 || job >= b->n) return set_error(BF_ERR_ARG, "job index out of range");
+    if (T < 0) return set_error(BF_ERR_ARG, "n_samp must be >= 0");
+    bf_plan *p = b->plans[job];
+    const int T_o = T / p->t_int;
+    if (T_o > 0 && (!x || !out)) return set_error(BF_ERR_ARG, "NULL voltage or output pointer");
+    if (((uintptr_t)x & 15) || ((uintptr_t)out & 15))
+        return set_error(BF_ERR_ARG, "voltages and powers must be 16-byte aligned");
+    if (b->launched) {
+        cudaError_t e = cudaStreamSynchronize(b->last_stream);   // the table may be read by a copy in flight
+        if (e != cudaSuccess) return cuda_error(e, "batch synchronize");
+    }
+    if (b->graph_exec) {   // a captured step refers to the old inputs
+        cudaGraphExecDestroy(b->graph_exec);
+        cudaGraphDestroy(b->graph);
+        b->graph_exec = nullptr;
+        b->graph = nullptr;
+    }
+    const WeightFormat &f = p->wf;
+    const void *xin = x;
+    const bool expand = p->dtype == BF_CI8 || p->dtype == BF_CI4;
+    if (expand && T_o > 0) {
+        const size_t need = (size_t)p->C * T * p->N * 4;
+        if (b->expand_bytes[job] < need) {
+            if (b->expand_buf[job]) cudaFree(b->expand_buf[job]);
+            b->expand_buf[job] = nullptr;
+            b->expand_bytes[job] = 0;
+            cudaError_t e = cudaMalloc(&b->expand_buf[job], need);
+            if (e != cudaSuccess) return cuda_error(e, "batch expansion buffer");
+            b->expand_bytes[job] = need;
+        }
+        xin = b->expand_buf[job];
+    }
+    BatchJob &J = b->h_jobs[job];
+    J.C = p->C;
+    J.t_tiles = (T_o * p->t_int + b->nt - 1) / b->nt;   // whole windows only
+    J.mt = f.m_pad / kRowsPerMTile;
+    J.kb = f.kb;
+    J.ke = f.ke;
+    J.w = f.kb + 1;
+    J.T = T;
+    J.T_o = T_o;
+    J.B = p->B;
+    J.b_pad = f.b_pad;
+    const uint32_t fmt = (f.op == kOpBF16) ? 1u : 0u;
+    J.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(b->nt >> 3) << 17) |
+              ((uint32_t)(kRowsPerMTile >> 4) << 24);
+    J.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;
+    J.wsig = p->d_wsig;
+    J.out = out;
+    J.units = T_o > 0 ? (long long)J.C * J.t_tiles * J.mt : 0;
+    if (J.units > 0) {
+        if (!encode_voltage_map(&J.xmap, xin, 2 * p->N, T, p->C, f.es, f.ke, b->nt))
+            return set_error(BF_ERR_ARG, "voltage tensor map rejected (pointer or row stride not 16-byte aligned?)");
+        if (!encode_weight_map(&J.wmap, p->d_w, f.k_pad, f.m_pad, p->C, f.es, f.ke))
+            return set_error(BF_ERR_CUDA, "weight tensor map rejected");
+    }
+    b->in[job] = x;
+    b->n_samp[job] = T;
+    b->out[job] = out;
+    b->set[job] = 1;
+    batch_reindex(b);
+    return BF_OK;
+}
+
+bf_status bf_batch_execute(bf_batch *b, void *stream)
+{
+    if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
+    for (int j = 0; j < b->n; ++j)
+        if (!b->set[j]) return set_error(BF_ERR_STATE, "every job needs bf_batch_set before execute");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->total_units == 0) return BF_OK;
+    b->last_stream = s;
+    b->launched = true;
+    cudaError_t e;
+    for (int j = 0; j < b->n; ++j) {
+        const bf_plan *p = b->plans[j];
+        if (b->h_jobs[j].units > 0 && (p->dtype == BF_CI8 || p->dtype == BF_CI4)) {
+            e = launch_expand_to_f16(b->in[j], p->dtype, b->expand_buf[j], (long long)p->C * b->n_samp[j] * p->N,
+                                     p->N, s);
+            if (e != cudaSuccess) return cuda_error(e, "integer expansion");
+        }
+    }
+    e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * b->n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "batch table upload");
+    BatchArgs ka;
+    ka.jobs = b->d_jobs;
+    ka.n_jobs = b->n;
+    ka.total_cost = b->total_cost;
+    ka.nt = b->nt;
+    ka.nsplit = b->nsplit;
+    ka.wpt = b->wpt;
+    ka.t_int = b->t_int;
+    ka.xst = b->xst;
+    ka.nacc = b->nacc;
+    ka.stage_bytes = (uint32_t)batch_stage_bytes(b->nt);
+    ka.err = b->d_err;
+    const int grid = (int)std::min<long long>(b->num_sms, b->total_units);
+    BF_BATCH_DISPATCH(BF_LAUNCH);
+    if (e != cudaSuccess) return cuda_error(e, "batched tensor-core kernel");
+    return BF_OK;
+}
+
+bf_status bf_batch_capture(bf_batch *b, void *stream)
+{
+    if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
+    if (!stream) return set_error(BF_ERR_ARG, "capture needs a non-default stream");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->graph_exec) {
+        cudaGraphExecDestroy(b->graph_exec);
+        cudaGraphDestroy(b->graph);
+        b->graph_exec = nullptr;
+        b->graph = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_error(e, "begin capture");
+    bf_status st = bf_batch_execute(b, stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (st != BF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "end capture");
+    e = cudaGraphInstantiate(&b->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_error(e, "graph instantiate");
+    }
+    b->graph = g;
+    return BF_OK;
+}
+
+bf_status bf_batch_replay(bf_batch *b, void *stream)
+{
+    if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
+    if (!b->graph_exec) return set_error(BF_ERR_STATE, "no captured step (bf_batch_capture first)");
+    cudaError_t e = cudaGraphLaunch(b->graph_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "graph launch");
+    b->last_stream = (cudaStream_t)stream;
+    b->launched = true;
+    return BF_OK;
+}
+
+bf_status bf_batch_sync(bf_batch *b)
+{
+    if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
+    cudaError_t e = b->launched ? cudaStreamSynchronize(b->last_stream) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_error(e, "batch synchronize");
+    unsigned err = 0;
+    e = cudaMemcpy(&err, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "read status word");
+    if (err) {
+        cudaMemset(b->d_err, 0, sizeof(unsigned));
+        return set_error(BF_ERR_TIMEOUT, "a device-side wait of the batched kernel timed out");
+    }
+    return BF_OK;
+}
+
+bf_status bf_batch_query(const bf_batch *b, int *tile_t, long long *units, double *flops)
+{
+    if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
+    if (tile_t) *tile_t = b->nt;
+    if (units) *units = b->total_units;
+    if (flops) *flops = b->flops;
+    return BF_OK;
+}
+
+bf_status bf_batch_destroy(bf_batch *b)
+{
+    batch_free(b);
+    return BF_OK;
+}
+
+}  // extern "C"

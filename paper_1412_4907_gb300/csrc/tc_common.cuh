@@ -1,0 +1,226 @@
+// Pieces shared by the single-plan and the batched tensor-core kernels:
+// constants, bounded drain wait, sums of squares, the per-tile epilogue
+// (TMEM accumulator -> |B|^2 -> window powers staged in shared memory, or
+// complex beams straight to HBM) and the store warp's per-tile write.
+#pragma once
+#include <cudaTypedefs.h>
+
+#include "bf_internal.h"
+#include "ptx.cuh"
+
+namespace bfi {
+
+constexpr int kEpiWarps = 8;
+constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
+constexpr int kTcThreads = (3 + kEpiWarps) * 32;
+constexpr int kStageDepth = 4;                     // staged tiles in flight
+constexpr int kTmemCols = 512;
+constexpr int kMaxWinPerTile = 16;
+constexpr int kMaxXStages = 8;
+constexpr int kMaxAcc = 8;                         // TMEM accumulators (512 columns / tile)
+constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
+
+// Bounded wait that ignores the abort flag (used only to drain on abort).
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 400000000ll) break;   // ~0.2 s
+}
+
+// Sum of squares of 16 values with four independent chains.
+__device__ __forceinline__ float sumsq16(const float *v)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+        s0 = fmaf(v[i], v[i], s0);
+        s1 = fmaf(v[i + 1], v[i + 1], s1);
+        s2 = fmaf(v[i + 2], v[i + 2], s2);
+        s3 = fmaf(v[i + 3], v[i + 3], s3);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+// Sum of squares of n (multiple of 8) raw FP32 values with packed FMAs in
+// four independent chains, combined in a fixed order.
+template <int n>
+__device__ __forceinline__ float sumsq_pk(const uint32_t *r)
+{
+    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) sq_acc2(acc[i & 3], r[2 * i], r[2 * i + 1]);
+    return (sum2(acc[0]) + sum2(acc[1])) + (sum2(acc[2]) + sum2(acc[3]));
+}
+
+// What the epilogue and the store warp need to know about the output of the
+// plan (or batched job) a tile belongs to.
+struct TileOut {
+    int nt, nsplit, wpt, t_int, T, T_o, B, b_pad, c_total;
+    const float *wscale;   // [C][b_pad] sigma^2, or NULL (unscaled)
+    const float *wsig;     // [C][b_pad] sigma
+    float *out;            // powers [B][C][T_o] or beams [B][C][T][2]
+};
+
+// Hand a TMEM accumulator back to the MMA issuer (after its loads completed).
+__device__ __forceinline__ void tile_release(uint32_t b_tempty_acc, int lane)
+{
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive_relaxed(b_tempty_acc);
+}
+
+// Power epilogue of one warp for one tile: read this warp's column slice of
+// the accumulator (32 rows = 16 beams x re/im), release the accumulator, sum
+// |B|^2 over each window in a fixed order, combine re and im rows with one
+// shuffle, scale, and stage the window powers for the store warp.
+// WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
+// -1 = any T_int (per-column window counter).
+template <int WIN>
+__device__ __forceinline__ void epi_power_tile(const TileOut &o, uint32_t taddr, int cols, int h, int lane, int bq,
+                                               int b, bool bvalid, int cg, float *stg, uint32_t b_tempty_acc,
+                                               uint32_t b_sfull_sb)
+{
+    const int part = (lane >> 4) & 1;   // 0: re row, 1: im row
+    const int wps = cols / o.t_int;     // windows per slice
+    const float scale = bvalid ? (o.wscale ? o.wscale[(size_t)cg * o.b_pad + b] : 1.f) : 0.f;
+    float ws = 0.f;
+    int wi = 0, cnt = 0;
+    auto emit = [&](float sum) {
+        const float pw = (sum + __shfl_xor_sync(0xffffffffu, sum, 16)) * scale;
+        if (part == 0) stg[bq * kMaxWinPerTile + h * wps + wi] = pw;
+        ++wi;
+    };
+    auto add16 = [&](const float *v) {
+        if (WIN >= 0) {
+            ws += sumsq16(v);
+            cnt += 16;
+            if (cnt == o.t_int) {
+                emit(ws);
+                ws = 0.f;
+                cnt = 0;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                ws = fmaf(v[i], v[i], ws);
+                if (++cnt == o.t_int) {
+                    emit(ws);
+                    ws = 0.f;
+                    cnt = 0;
+                }
+            }
+        }
+    };
+    int col = 0;
+    if (WIN > 0 && cols == 64) {
+        uint32_t r[64];
+        tmem_ld64r(taddr, r);
+        tile_release(b_tempty_acc, lane);
+#pragma unroll
+        for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
+            emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
+        col = 64;
+    } else if (WIN > 0 && cols % 128 == 0) {
+        // 128 columns per load; the accumulator is released after the last
+        // load, before the squares are summed
+        for (; col < cols; col += 128) {
+            uint32_t r[128];
+            tmem_ld128(taddr + col, r);
+            if (col + 128 == cols) tile_release(b_tempty_acc, lane);
+#pragma unroll
+            for (int k = 0; k < 128 / (WIN > 0 ? WIN : 128); ++k)
+                emit(sumsq_pk<(WIN > 0 ? WIN : 128)>(r + k * (WIN > 0 ? WIN : 128)));
+        }
+    }
+    const int n64 = (cols - col) / 64, rem = (cols - col) % 64;   // rem is a multiple of 16
+    for (int bt = 0; bt < n64; ++bt) {
+        float v[64];
+        tmem_ld64(taddr + col + bt * 64, v);
+        if (bt == n64 - 1 && rem == 0) tile_release(b_tempty_acc, lane);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) add16(v + 16 * k);
+    }
+    for (col += n64 * 64; col < cols; col += 16) {
+        float v[16];
+        tmem_ld16(taddr + col, v);
+        if (col + 16 == cols) tile_release(b_tempty_acc, lane);
+        add16(v);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b_sfull_sb);   // publishes the staged windows
+}
+
+// Complex-beam epilogue of one warp for one tile: beams straight to HBM.
+__device__ __forceinline__ void epi_complex_tile(const TileOut &o, uint32_t taddr, int cols, int col0, int tt,
+                                                 int lane, int b, bool bvalid, int cg)
+{
+    const int part = (lane >> 4) & 1;
+    const float sg = bvalid ? o.wsig[(size_t)cg * o.b_pad + b] : 0.f;
+    float2 *o2 = reinterpret_cast<float2 *>(o.out);
+    const size_t ob = ((size_t)b * o.c_total + cg) * o.T;
+    for (int ch = 0; ch < cols / 16; ++ch) {
+        float v[16], x[16];
+        tmem_ld16(taddr + ch * 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = __shfl_xor_sync(0xffffffffu, v[i], 16);
+        const int t0 = tt * o.nt + col0 + ch * 16;
+        // lanes 0-15 hold the re row and store samples 0-7 of the chunk;
+        // lanes 16-31 hold the im row and store samples 8-15
+        if (bvalid && part == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (t0 + i < o.T) o2[ob + t0 + i] = make_float2(v[i] * sg, x[i] * sg);
+        } else if (bvalid) {
+#pragma unroll
+            for (int i = 8; i < 16; ++i)
+                if (t0 + i < o.T) o2[ob + t0 + i] = make_float2(x[i] * sg, v[i] * sg);
+        }
+    }
+}
+
+// The store warp's write of one staged tile: one run of windows per beam.
+__device__ __forceinline__ void store_tile(const TileOut &o, const float *stg, int b_tile0, int cg, int tt, int lane)
+{
+    const bool vec = (o.T_o & 3) == 0 && (o.wpt & 3) == 0;
+    const int j0 = tt * o.wpt;
+    const int nj = min(o.wpt, o.T_o - j0);
+    if (vec && o.wpt == 4) {
+        // one float4 per beam: lanes take beams lane and lane + 32
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int bl = lane + 32 * r;
+            const int bb = b_tile0 + bl;
+            if (bb < o.B && nj > 0) {
+                const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile);
+                *reinterpret_cast<float4 *>(o.out + ((size_t)bb * o.c_total + cg) * o.T_o + j0) = v4;
+            }
+        }
+    } else if (vec) {
+        const int per = o.wpt >> 2;
+        for (int i = lane; i < kBeamsPerMTile * per; i += 32) {
+            const int bl = i / per, k = (i % per) * 4;
+            const int bb = b_tile0 + bl;
+            if (bb < o.B && k < nj) {
+                const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile + k);
+                *reinterpret_cast<float4 *>(o.out + ((size_t)bb * o.c_total + cg) * o.T_o + j0 + k) = v4;
+            }
+        }
+    } else {
+        for (int i = lane; i < kBeamsPerMTile * o.wpt; i += 32) {
+            const int bl = i / o.wpt, k = i % o.wpt;
+            const int bb = b_tile0 + bl;
+            if (bb < o.B && k < nj) o.out[((size_t)bb * o.c_total + cg) * o.T_o + j0 + k] = stg[bl * kMaxWinPerTile + k];
+        }
+    }
+}
+
+// Host: the driver's tensor-map encoder (fetched once through the runtime).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+// Host: K-major 3-D tensor maps with the 128-byte swizzle: voltages
+// [C][T][2N] (box ke x nt x 1) and weight rows [C][M_pad][K_pad] (box ke x 128 x 1).
+bool encode_voltage_map(CUtensorMap *m, const void *x, int two_n, int T, int C, int es, int ke, int nt);
+bool encode_weight_map(CUtensorMap *m, const void *w, int k_pad, int m_pad, int C, int es, int ke);
+
+}  // namespace bfi

@@ -79,6 +79,15 @@ def test_null_and_bad_handles(bf):
     assert lib.bf_execute(None, None, 0, None, None) == bf.BF_ERR_ARG
     assert lib.bf_weights(None, None) == bf.BF_ERR_ARG
     assert lib.bf_plan_query(None, None, None, None, None) == bf.BF_ERR_ARG
+    b = ctypes.c_void_p()
+    assert lib.bf_batch_create(ctypes.byref(b), None, 0, 0) == bf.BF_ERR_ARG
+    assert lib.bf_batch_create(None, None, 1, 0) == bf.BF_ERR_ARG
+    assert lib.bf_batch_set(None, 0, None, 0, None) == bf.BF_ERR_ARG
+    assert lib.bf_batch_execute(None, None) == bf.BF_ERR_ARG
+    assert lib.bf_batch_replay(None, None) == bf.BF_ERR_ARG
+    assert lib.bf_batch_sync(None) == bf.BF_ERR_ARG
+    assert lib.bf_batch_query(None, None, None, None) == bf.BF_ERR_ARG
+    assert lib.bf_batch_destroy(None) == bf.BF_OK
     out = ctypes.c_void_p(123)
     assert lib.bf_plan_create(ctypes.byref(out), 0, None, None, 0, None, 0, None, 0, 0, 0, None) == bf.BF_ERR_ARG
     assert out.value is None
