@@ -426,6 +426,305 @@ def run_sweep(args):
         print(json.dumps(line), flush=True)
 
 
+def config4_inputs(jobs, torch, device="cuda"):
+    """Seeded FP16 voltages [C][T][2N] of the batched workload, made on the
+    device (74 GB in all: too much to build on the host in a bench run):
+    complex Gaussian noise (sigma 1/sqrt(2) per component) plus one plane
+    wave per job (SNR 10 dB per antenna and sample, noise-like signal,
+    phase exp(+i 2 pi f_c r_n . s / c0))."""
+    xs = []
+    c0 = 299792458.0
+    for j, job in enumerate(jobs):
+        N, C, T = job.scene.pos.shape[0], job.scene.freqs.size, job.scene.n_samp
+        g = torch.Generator(device=device)
+        g.manual_seed(4_000_000 + j)
+        x = torch.empty((C, T, 2 * N), dtype=torch.float16, device=device)
+        src = job.scene.sources[0]
+        a = float(np.sqrt(src.power / 2.0))                           # CN(0, power) per sample
+        tau = job.scene.pos @ src.dir / c0                             # [N] seconds
+        for c0_ in range(0, C, 64):
+            c1 = min(C, c0_ + 64)
+            ph = np.outer(job.scene.freqs[c0_:c1], tau)                # [c][N] cycles
+            ph = torch.from_numpy(np.exp(2j * np.pi * (ph - np.rint(ph))).astype(np.complex64)).to(device)
+            s = torch.randn((c1 - c0_, T, 2), generator=g, device=device) * a
+            s = torch.view_as_complex(s)                               # [c][T]
+            n = torch.randn((c1 - c0_, T, N, 2), generator=g, device=device) * 0.7071067811865476
+            v = torch.view_as_real(s[:, :, None] * ph[:, None, :]) + n
+            x[c0_:c1] = v.reshape(c1 - c0_, T, 2 * N).half()
+        xs.append(x)
+    return xs
+
+
+def run_batched(args):
+    """Config 4: 48 sub-array jobs of uneven size (N in {16..256}, B
+    log-uniform in 8..4096, C in {128, 512, 2048}, T = 4096, FP16, T_int 64)
+    in one graph-captured persistent launch.  One JSON line per variant:
+    fixed 128-sample tiles, the autotuned tile width, and the jobs run one
+    plan at a time through bf_execute (each with the single-plan planner's
+    tiling); plus the power error on sampled channels against the oracle."""
+    import torch
+
+    import oracle
+    import paper_1412_4907_gb300 as bf
+    from paper_1412_4907_gb300 import tune
+    torch.cuda.set_device(0)
+    jobs = synth.config4_jobs()
+    stream = torch.cuda.Stream()
+    plans, outs, n_samps = [], [], []
+    F = 0.0
+    for job in jobs:
+        N, B, C, T = job.scene.pos.shape[0], job.dirs.shape[0], job.scene.freqs.size, job.scene.n_samp
+        plans.append(bf.Plan(job.scene.pos, job.scene.freqs, job.dirs, bf.BF_C16F, job.t_int, stream=stream))
+        outs.append(torch.empty((B, C, T // job.t_int), dtype=torch.float32, device="cuda"))
+        n_samps.append(T)
+        F += flops(N, B, C, T)
+    xs = config4_inputs(jobs, torch)
+    torch.cuda.synchronize()
+    pk, pk_kind = peaks()
+    peak = pk["bf16_tflops_sustained"]
+    steps = max(3, min(args.steps, 20))
+    warm = max(3, min(args.warmup, 5))
+
+    def timed(run):
+        for _ in range(warm):
+            run()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            run()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / steps
+
+    def line(variant, ms, extra):
+        tf = F / (ms * 1e-3) / 1e12
+        d = {"metric": "batched uneven launch: beamform TFLOP/s", "variant": variant, "value": tf, "unit": UNIT,
+             "ms_per_step": ms, "steps": steps, "warmup": warm, "dtype": "f16", "data": "synthetic",
+             "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                          "peak_source": f"bf16_tflops_sustained {pk_kind}"},
+             "config": {"workload": "48 sub-array jobs: N in {16,32,64,128,256} of the 256-antenna 200 m layout, "
+                                    "B log-uniform 8..4096, C in {128,512,2048}, T 4096 FP16, T_int 64",
+                        "total_tflop": F / 1e12, "jobs": len(jobs),
+                        "l2": "no flush: 74 GB of voltages and 21 GB of weights per step exceed the 129 MB L2"}}
+        d.update(extra)
+        print(json.dumps(d), flush=True)
+
+    # fixed tiles
+    batch = bf.Batch(plans, tile_t=128, stream=stream)
+    for j, (x, o, T) in enumerate(zip(xs, outs, n_samps)):
+        batch.set(j, x, o, n_samp=T)
+    batch.capture()
+    ms_fixed = timed(batch.replay)
+    batch.sync()
+    line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": 1})
+    batch.close()
+    # autotuned
+    tuned = tune.tune_batch(plans, xs, outs, n_samps, stream=stream, reps=3, cache=None)
+    batch = bf.Batch(plans, tile_t=tuned["tile_t"], stream=stream)
+    for j, (x, o, T) in enumerate(zip(xs, outs, n_samps)):
+        batch.set(j, x, o, n_samp=T)
+    batch.capture()
+    ms_tuned = timed(batch.replay)
+    batch.sync()
+    line("batched, autotuned tile", ms_tuned, {"tile_t": tuned["tile_t"], "tuning_table": tuned["table"],
+                                                "speedup_vs_fixed": ms_fixed / ms_tuned, "gpu_launches_per_step": 1})
+    # one plan at a time
+    def per_plan():
+        for p, x, o, T in zip(plans, xs, outs, n_samps):
+            bf.bf_execute(p.handle, x.data_ptr(), T, o.data_ptr(), stream.cuda_stream)
+    ms_seq = timed(per_plan)
+    line("one launch per job (bf_execute)", ms_seq, {"gpu_launches_per_step": len(plans),
+                                                     "batched_speedup": ms_seq / ms_tuned})
+    # parity on sampled channels of four jobs (batched, autotuned outputs)
+    batch.replay()
+    batch.sync()
+    errs = []
+    order = sorted(range(len(jobs)), key=lambda j: plans[j].N * plans[j].B)
+    for j in (order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]):
+        job, p = jobs[j], plans[j]
+        c = p.C // 2
+        xh = xs[j][c:c + 1].cpu().numpy().view(np.float16)
+        X64 = oracle.decode_voltages(synth.C16F, xh)
+        W = oracle.weights(job.scene.pos, job.scene.freqs[c:c + 1], job.dirs)
+        Wq = oracle.quantised_weights(W, synth.C16F)[0]
+        Pref = oracle.power(Wq, X64, job.t_int)
+        mx, l2 = power_errors(outs[j][:, c:c + 1, :].cpu().numpy(), Pref)
+        errs.append({"job": j, "N": p.N, "B": p.B, "channel": c, "max_rel": mx, "l2_rel": l2})
+    batch.close()
+    print(json.dumps({"metric": "batched uneven launch: power error vs FP64 oracle (same FP16 inputs and weights)",
+                      "samples": errs}), flush=True)
+
+
+SERVE_CONFIGS = [(32, 1024, 1024, synth.C16F), (64, 64, 4096, synth.CI8), (128, 512, 2048, synth.C16F),
+                 (256, 2048, 512, synth.CI8), (512, 8192, 256, synth.C16F), (512, 256, 4096, synth.CI8)]
+SERVE_RATE_HZ = 1024          # samples per second per channel: a chunk of d seconds has round(1024 d) samples
+
+
+def serve_plans(bf, stream, mode_override=None):
+    plans = []
+    for i, (N, B, C, mode) in enumerate(SERVE_CONFIGS):
+        pos = synth.grid_positions() if N == 32 else synth.random_positions(N, 200.0, 500 + i)
+        nx = int(round(np.sqrt(B)))
+        dirs = synth.beam_grid(nx, -(-B // nx))[:B]
+        freqs = synth.channel_freqs(400e6, 16e6, C)
+        plans.append(bf.Plan(pos, freqs, dirs, mode if mode_override is None else mode_override, 64, stream=stream))
+    return plans
+
+
+def serve_arrivals(rate, seconds, seed=5):
+    """Poisson arrivals: (time offset s, config, samples per channel)."""
+    g = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += g.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        cfg = int(g.integers(0, len(SERVE_CONFIGS)))
+        T = int(round(g.uniform(0.25, 1.0) * SERVE_RATE_HZ))
+        out.append((t, cfg, T))
+
+
+def serve_pool(torch, mode, N, C, T, seed):
+    """One pinned host chunk [C][T][N] of the mode's dtype (seeded noise made
+    on the device: FP16 sigma 1/sqrt(2) per component, int8 sigma 16 clipped)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    v = torch.randn((C, T, 2 * N), generator=g, device="cuda")
+    if mode == synth.CI8:
+        v = torch.clamp(torch.round(v * 16.0), -127, 127).to(torch.int8)
+    else:
+        v = (v * 0.7071067811865476).to(torch.float16 if mode == synth.C16F else torch.float32)
+    h = torch.empty(v.shape, dtype=v.dtype).pin_memory()
+    h.copy_(v)
+    return h
+
+
+def pct(a, q):
+    return float(np.percentile(np.asarray(a), q)) if len(a) else None
+
+
+def run_serve(args):
+    """Config 5: Poisson arrivals (default 400 chunks/s) of 0.25-1 s chunks
+    from 6 streams (32-512 antennas, 64-8192 beams, 256-4096 channels, FP16 or
+    int8), served by bf_server: latency from arrival on the host to powers in
+    host memory (p50/p99), sustained and device-only TFLOP/s; then the plain
+    FP32 single-job path (bf_execute_host, one chunk at a time) on the first
+    chunks of the same arrival list."""
+    import torch
+
+    import paper_1412_4907_gb300 as bf
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    plans = serve_plans(bf, stream)
+    pools, rings = [], []
+    for i, (N, B, C, mode) in enumerate(SERVE_CONFIGS):
+        pools.append(serve_pool(torch, mode, N, C, SERVE_RATE_HZ, 5000 + i))
+        rings.append([torch.empty(B * C * (SERVE_RATE_HZ // 64 + 1), dtype=torch.float32).pin_memory()
+                      for _ in range(4)])
+    torch.cuda.synchronize()
+    server = bf.Server(plans, mem_bytes=int(args.serve_mem * 2**30), max_steps=3)
+    for i in range(len(SERVE_CONFIGS)):   # warm-up: one chunk per stream
+        server.submit(i, pools[i], rings[i][0], n_samp=256)
+    server.drain(120000)
+    server.poll(64)
+    base = server.stats()
+    arrivals = serve_arrivals(args.serve_rate, args.serve_seconds)
+    t0 = bf.bf_server_now() + 0.05
+    ids = {}
+    for k, (ta, cfg, T) in enumerate(arrivals):
+        due = t0 + ta
+        while True:
+            d = due - bf.bf_server_now()
+            if d <= 0:
+                break
+            if d > 0.002:
+                time.sleep(d - 0.001)
+        i = server.submit(cfg, pools[cfg], rings[cfg][k % 4], n_samp=T)
+        ids[i] = (due, cfg, T)
+    t_sub_end = bf.bf_server_now()
+    server.drain(600000)
+    done = {}
+    while len(done) < len(ids):
+        for c in server.poll(1024, 1000):
+            done[c["id"]] = c
+    st = server.stats()
+    server.close()
+    lat, lat_dev, per_cfg = [], [], {}
+    t_last = t0
+    F = 0.0
+    h2d = 0
+    for i, (due, cfg, T) in ids.items():
+        c = done[i]
+        assert c["status"] == 0, c
+        lat.append(c["t_done"] - due)
+        lat_dev.append(c["t_done"] - c["t_start"])
+        per_cfg.setdefault(cfg, []).append(c["t_done"] - due)
+        t_last = max(t_last, c["t_done"])
+        N, B, C, mode = SERVE_CONFIGS[cfg]
+        F += flops(N, B, C, T)
+        h2d += C * T * N * (4 if mode == synth.C16F else 2)
+    kernel_ms = st["kernel_ms"] - base["kernel_ms"]
+    steps = st["steps"] - base["steps"]
+    sustained = F / (t_last - t0) / 1e12
+    pk, pk_kind = peaks()
+    res = {"metric": "serving stream: p50/p99 chunk latency and sustained TFLOP/s", "value": sustained,
+           "unit": UNIT, "higher_is_better": True, "dtype": "f16 (int8 inputs widened to f16)", "data": "synthetic",
+           "chunks": len(ids), "seconds_offered": args.serve_seconds, "rate_hz": args.serve_rate,
+           "latency_ms": {"p50": 1e3 * pct(lat, 50), "p99": 1e3 * pct(lat, 99), "mean": 1e3 * float(np.mean(lat)),
+                          "max": 1e3 * float(np.max(lat))},
+           "latency_from_step_start_ms": {"p50": 1e3 * pct(lat_dev, 50), "p99": 1e3 * pct(lat_dev, 99)},
+           "latency_p99_ms_per_config": {str(k): 1e3 * pct(v, 99) for k, v in sorted(per_cfg.items())},
+           "offered_tflops": F / args.serve_seconds / 1e12, "device_tflops": F / (kernel_ms * 1e-3) / 1e12,
+           "device_busy_frac": kernel_ms * 1e-3 / (t_last - t0),
+           "roofline": {"bound": "tensor", "achieved": F / (kernel_ms * 1e-3) / 1e12, "peak": pk["bf16_tflops_sustained"],
+                        "unit": "TFLOP/s", "frac": F / (kernel_ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"],
+                        "peak_source": f"bf16_tflops_sustained {pk_kind}"},
+           "h2d_gbps_offered": h2d / args.serve_seconds / 1e9, "h2d_gbps_achieved": h2d / (t_last - t0) / 1e9,
+           "steps": steps, "mean_chunks_per_step": len(ids) / max(1, steps), "max_chunks_per_step": st["max_jobs_per_step"],
+           "arena_gb": st["arena_bytes"] / 2**30, "arena_peak_gb": st["arena_peak"] / 2**30,
+           "submit_lag_s": t_sub_end - (t0 + arrivals[-1][0]) if arrivals else 0.0,
+           "config": {"workload": "6 streams (32,1024,1024,f16) (64,64,4096,i8) (128,512,2048,f16) (256,2048,512,i8) "
+                                  "(512,8192,256,f16) (512,256,4096,i8) as (N,B,C,dtype); Poisson arrivals, chunk "
+                                  "0.25-1 s at 1024 samples/s per channel, T_int 64 with the open window carried",
+                      "tile_t": st["tile_t"]}}
+    print(json.dumps(res), flush=True)
+    for p in plans:
+        p.close()
+    del pools, rings
+    torch.cuda.synchronize()
+    if args.no_fp32_form:
+        return
+    # the plain FP32 single-job path on the first chunks of the same list
+    plans32 = serve_plans(bf, torch.cuda.current_stream(), mode_override=synth.C32)
+    n32 = min(len(arrivals), args.serve_fp32_chunks)
+    need = max(C * T * N for (_, cfg, T) in arrivals[:n32] for (N, _, C, _) in [SERVE_CONFIGS[cfg]])
+    xh = torch.empty(2 * need, dtype=torch.float32).pin_memory()
+    xh.normal_(0.0, 0.7071067811865476)
+    outh = torch.empty(max(B * C * (SERVE_RATE_HZ // 64 + 1) for (_, B, C, _) in SERVE_CONFIGS),
+                       dtype=torch.float32).pin_memory()
+    for i in range(len(plans32)):   # warm-up
+        bf.bf_execute_host(plans32[i].handle, xh.data_ptr(), 64, outh.data_ptr())
+    svc, F32 = [], 0.0
+    t_start = time.perf_counter()
+    for (_, cfg, T) in arrivals[:n32]:
+        a = time.perf_counter()
+        bf.bf_execute_host(plans32[cfg].handle, xh.data_ptr(), T, outh.data_ptr())
+        svc.append(time.perf_counter() - a)
+        N, B, C, _ = SERVE_CONFIGS[cfg]
+        F32 += flops(N, B, C, T)
+    busy = time.perf_counter() - t_start
+    offered32 = F32 / (arrivals[n32 - 1][0] if n32 else 1.0)
+    print(json.dumps({"metric": "serving stream: plain FP32 single-job path (bf_execute_host, one chunk at a time)",
+                      "value": F32 / busy / 1e12, "unit": UNIT, "dtype": "f32", "chunks": n32,
+                      "service_ms": {"p50": 1e3 * pct(svc, 50), "p99": 1e3 * pct(svc, 99)},
+                      "offered_tflops": offered32 / 1e12,
+                      "note": "back to back with no queueing: service time is a lower bound on its latency; "
+                              "at the offered rate its queue grows without bound when offered > value"}), flush=True)
+    for p in plans32:
+        p.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,6 +736,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="precision sweep on the config-3 shape (one JSON line per mode) instead of the benchmark")
+    ap.add_argument("--batched", action="store_true",
+                    help="batched uneven launch of 48 sub-array jobs (one JSON line per variant)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving stream of 6 configurations with Poisson arrivals (p50/p99 latency)")
+    ap.add_argument("--serve-rate", type=float, default=400.0, help="chunk arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="seconds of arrivals")
+    ap.add_argument("--serve-mem", type=float, default=48.0, help="server arena in GiB")
+    ap.add_argument("--serve-fp32-chunks", type=int, default=40, help="chunks for the FP32 single-job comparison")
     ap.add_argument("--channels", type=int, default=0,
                     help="run only the first C channels (same per-channel shape; for profiling)")
     args = ap.parse_args()
@@ -445,6 +752,10 @@ def main():
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.batched:
+        run_batched(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -269,8 +269,8 @@ typedef struct bf_batch bf_batch;
  * bf_batch_create — batch over plans[0 .. n_plans-1] (host array, read
  * during the call).  tile_t = 0 chooses the widest tile (samples per MMA, a
  * multiple of 16 and of T_int, at most 256 and 16 windows); otherwise that
- * width.  Allocates the device job table (one 256-byte entry per plan) and a
- * pinned host copy.  Errors: BF_ERR_ARG (NULL or empty), BF_ERR_UNSUPPORTED
+ * width.  Allocates the device job table (one entry per plan) and a pinned
+ * host copy.  Errors: BF_ERR_ARG (NULL or empty), BF_ERR_UNSUPPORTED
  * (plans that cannot share a launch, no tile width fits), BF_ERR_NOMEM /
  * BF_ERR_CUDA.
  */
@@ -317,6 +317,102 @@ bf_status bf_batch_query(const bf_batch *batch, int *tile_t, long long *units, d
 /* bf_batch_destroy — wait for the last step and free the batch (not the
  * plans).  NULL is a no-op. */
 bf_status bf_batch_destroy(bf_batch *batch);
+
+/*
+ * Serving: a real-time loop over voltage chunks of several streams.
+ *
+ * Each stream is one configuration (a plan: sub-array, beams, channels,
+ * dtype); its chunks are consecutive pieces of one voltage stream [C][T][N]
+ * (CTN, the plan's dtype) of any length.  Chunks are submitted from host
+ * memory as they arrive; a scheduler thread admits them into a device arena
+ * of fixed size as memory frees up, runs each step (at most one chunk per
+ * stream, any mix of streams) as one batched tensor-core launch, overlaps the
+ * copies of the next step with the current launch, and copies the powers back
+ * into host memory.  The weights (in the plans) and the open integration
+ * window of every stream stay on the device: a chunk completes the window the
+ * previous chunk of its stream left open (Section 2.1 integration across
+ * buffer boundaries, Section 3 real-time operation), so a stream integrates
+ * the same whatever its cut into chunks.
+ *
+ * The plans must satisfy the bf_batch_create rules; additionally N * 2 *
+ * (bytes per MMA operand element: 2 for 16-bit and widened integer inputs,
+ * 1 for FP8) must be a multiple of 16.  The server keeps pointers to the
+ * plans; they must outlive it and must not be re-pointed while it runs.
+ */
+typedef struct bf_server bf_server;
+
+/* One finished chunk.  Times are seconds on the host steady clock
+ * (bf_server_now). */
+typedef struct bf_completion {
+    long long id;        /* as returned by bf_server_submit */
+    int config;          /* stream index */
+    int status;          /* bf_status of the chunk */
+    int n_windows;       /* windows completed by this chunk: h_power holds [B][C][n_windows] */
+    int step;            /* scheduler step that computed it */
+    int n_samp;          /* samples per channel in the chunk */
+    double t_submit;     /* bf_server_submit returned */
+    double t_start;      /* its step's copies were enqueued */
+    double t_done;       /* its powers were in host memory */
+} bf_completion;
+
+typedef struct bf_server_counters {
+    long long submitted, completed, steps;
+    int max_jobs_per_step;
+    int tile_t;
+    double flops;        /* 8 N B C T summed over completed chunks */
+    double kernel_ms;    /* device time of the batched launches (CUDA events) */
+    size_t arena_bytes, arena_peak;
+} bf_server_counters;
+
+/*
+ * bf_server_create — server over plans[0 .. n_configs-1] (host array, read
+ * during the call).  mem_bytes: device arena for admitted chunks (voltages,
+ * FP16 widening of integer inputs, powers); a chunk waits until its block
+ * fits.  max_steps (1..8): steps in flight at once.  tile_t as
+ * bf_batch_create.  Waits for the plans' weights, allocates the arena and
+ * two [B][C] float accumulators per stream, starts the scheduler thread.
+ */
+bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs, size_t mem_bytes,
+                           int max_steps, int tile_t);
+
+/*
+ * bf_server_submit — queue a chunk of stream `config`:
+ *  h_voltages  host, [C][n_samp][N] samples of the plan's dtype (page-locked
+ *              memory lets the copy run asynchronously), read until the chunk
+ *              completes;
+ *  h_power     host, room for [B][C][ceil(n_samp / T_int)] floats, written
+ *              before the completion is reported;
+ *  id          out (may be NULL): the chunk's id.
+ * Thread-safe.  Errors: BF_ERR_ARG (bad config, n_samp < 1, a chunk that
+ * could never fit the arena), BF_ERR_STATE (shutting down).
+ */
+bf_status bf_server_submit(bf_server *server, int config, const void *h_voltages, int n_samp,
+                           float *h_power, long long *id);
+
+/* bf_server_pause — paused != 0: admit nothing until resumed (submitted
+ * chunks queue; steps already enqueued finish), for instance to hold
+ * dispatch while the caller prepares a burst.  bf_server_destroy resumes. */
+bf_status bf_server_pause(bf_server *server, int paused);
+
+/* bf_server_poll — move up to `max` completions (oldest first) into out[],
+ * their count into *n_out; waits up to timeout_ms for the first one. */
+bf_status bf_server_poll(bf_server *server, bf_completion *out, int max, int *n_out, int timeout_ms);
+
+/* bf_server_drain — wait up to timeout_ms until every submitted chunk has
+ * completed.  BF_ERR_TIMEOUT if some have not; BF_ERR_CUDA if the scheduler
+ * met a CUDA error (the chunks concerned complete with that status). */
+bf_status bf_server_drain(bf_server *server, int timeout_ms);
+
+/* bf_server_stats — counters since creation (chunks, steps, FLOPs, device
+ * time, arena use). */
+bf_status bf_server_stats(bf_server *server, bf_server_counters *out);
+
+/* bf_server_destroy — finish every queued chunk, stop the scheduler, free
+ * the server (not the plans).  Completions not polled are discarded. */
+bf_status bf_server_destroy(bf_server *server);
+
+/* bf_server_now — the host steady clock of bf_completion, in seconds. */
+double bf_server_now(void);
 
 /*
  * bf_execute_nct_static — bf_execute for an antenna-major (BF_LAYOUT_NCT)

@@ -31,6 +31,19 @@ STATUS_NAMES = {0: "BF_OK", 1: "BF_ERR_ARG", 2: "BF_ERR_NOMEM", 3: "BF_ERR_CUDA"
 
 # every entry point declared in include/bf.h, with its ctypes signature
 _P, _I, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+
+
+class bf_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("config", ctypes.c_int), ("status", ctypes.c_int),
+                ("n_windows", ctypes.c_int), ("step", ctypes.c_int), ("n_samp", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class bf_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+                ("max_jobs_per_step", ctypes.c_int), ("tile_t", ctypes.c_int), ("flops", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("arena_bytes", ctypes.c_size_t), ("arena_peak", ctypes.c_size_t)]
+
 SIGNATURES = {
     "bf_plan_create": [ctypes.POINTER(_P), _I, _P, _P, _I, _P, _I, _P, _I, _I, _I, _P],
     "bf_weights": [_P, _P],
@@ -56,6 +69,14 @@ SIGNATURES = {
     "bf_batch_sync": [_P],
     "bf_batch_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
     "bf_batch_destroy": [_P],
+    "bf_server_create": [ctypes.POINTER(_P), _P, _I, _S, _I, _I],
+    "bf_server_submit": [_P, _I, _P, _I, _P, ctypes.POINTER(ctypes.c_longlong)],
+    "bf_server_poll": [_P, ctypes.POINTER(bf_completion), _I, ctypes.POINTER(_I), _I],
+    "bf_server_drain": [_P, _I],
+    "bf_server_pause": [_P, _I],
+    "bf_server_stats": [_P, ctypes.POINTER(bf_server_counters)],
+    "bf_server_destroy": [_P],
+    "bf_server_now": [],
     "bf_execute_nct_static": [_P, _P, _I, _P, _P],
 }
 
@@ -73,7 +94,7 @@ def _load():
     for name, argtypes in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = argtypes
-        fn.restype = ctypes.c_char_p if name == "bf_last_error" else ctypes.c_int
+        fn.restype = {"bf_last_error": ctypes.c_char_p, "bf_server_now": ctypes.c_double}.get(name, ctypes.c_int)
     return lib
 
 
@@ -216,6 +237,51 @@ def bf_batch_destroy(batch: int):
     _check(_lib.bf_batch_destroy(batch))
 
 
+def bf_server_create(plans, mem_bytes: int, max_steps: int = 3, tile_t: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = ctypes.c_void_p()
+    _check(_lib.bf_server_create(ctypes.byref(h), arr, len(plans), mem_bytes, max_steps, tile_t))
+    return h.value
+
+
+def bf_server_submit(server: int, config: int, h_voltages: int, n_samp: int, h_power: int) -> int:
+    i = ctypes.c_longlong()
+    _check(_lib.bf_server_submit(server, config, h_voltages, n_samp, h_power, ctypes.byref(i)))
+    return i.value
+
+
+_COMPLETION_FIELDS = [f for f, _ in bf_completion._fields_]
+
+
+def bf_server_poll(server: int, max_n: int = 256, timeout_ms: int = 0) -> list:
+    buf = (bf_completion * max_n)()
+    n = ctypes.c_int()
+    _check(_lib.bf_server_poll(server, buf, max_n, ctypes.byref(n), timeout_ms))
+    return [{f: getattr(buf[i], f) for f in _COMPLETION_FIELDS} for i in range(n.value)]
+
+
+def bf_server_pause(server: int, paused: bool = True):
+    _check(_lib.bf_server_pause(server, int(bool(paused))))
+
+
+def bf_server_drain(server: int, timeout_ms: int = 60000):
+    _check(_lib.bf_server_drain(server, timeout_ms))
+
+
+def bf_server_stats(server: int) -> dict:
+    c = bf_server_counters()
+    _check(_lib.bf_server_stats(server, ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in bf_server_counters._fields_}
+
+
+def bf_server_destroy(server: int):
+    _check(_lib.bf_server_destroy(server))
+
+
+def bf_server_now() -> float:
+    return _lib.bf_server_now()
+
+
 # ------------------------------------------------------------ torch helper
 class Plan:
     """A beamforming plan on the current CUDA device.  Voltages are torch
@@ -356,6 +422,52 @@ class Batch:
         if self.handle:
             bf_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop over several plans (``bf_server_*``).  ``submit`` takes a
+    host tensor of one chunk (page-locked for asynchronous copies) and a host
+    float32 tensor with room for [B][C][ceil(T / T_int)] powers; both must
+    stay alive until the chunk's completion has been polled."""
+
+    def __init__(self, plans, mem_bytes: int, max_steps: int = 3, tile_t: int = 0):
+        self.plans = list(plans)
+        self.handle = bf_server_create([p.handle for p in self.plans], int(mem_bytes), max_steps, tile_t)
+        self._live = {}
+
+    def submit(self, config: int, x_host, out_host, n_samp=None) -> int:
+        p = self.plans[config]
+        T = p.n_samp(x_host) if n_samp is None else n_samp
+        i = bf_server_submit(self.handle, config, x_host.data_ptr(), T, out_host.data_ptr())
+        self._live[i] = (x_host, out_host)
+        return i
+
+    def poll(self, max_n: int = 256, timeout_ms: int = 0) -> list:
+        done = bf_server_poll(self.handle, max_n, timeout_ms)
+        for c in done:
+            self._live.pop(c["id"], None)
+        return done
+
+    def drain(self, timeout_ms: int = 60000):
+        bf_server_drain(self.handle, timeout_ms)
+
+    def pause(self, paused: bool = True):
+        bf_server_pause(self.handle, paused)
+
+    def stats(self) -> dict:
+        return bf_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            bf_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
 
     def __del__(self):
         try:

@@ -1,0 +1,60 @@
+// Internal interface of the batched tensor-core launch, shared by the
+// bf_batch_* calls and the serving loop (bf_server_*).
+//
+// A launch walks a table of jobs.  Each job is one chunk of one plan: its
+// voltages [C][T][2N] (TMA tensor map), the plan's weight rows (tensor map),
+// per-beam scales and the output powers.  A job may continue an integration
+// that the previous chunk of the same stream left open: the first t_shift
+// samples of its first window belong to that chunk and their partial sum
+// arrives in acc_in; a window that this chunk leaves open is written, as a
+// partial sum, to acc_out instead of the output (Section 2.1 integration,
+// carried across chunk boundaries).
+#pragma once
+#include <cudaTypedefs.h>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+struct __align__(128) BatchJob {
+    CUtensorMap xmap;   // voltages [C][T][2N]
+    CUtensorMap wmap;   // weight rows [C][M_pad][K_pad]
+    long long unit0;    // first global unit of the job
+    long long units;    // C x t_tiles x mt
+    int C, t_tiles, mt, kb, ke;
+    int T, T_o, B, b_pad;
+    int t_shift;        // samples of window 0 that precede this chunk (0..T_int-1)
+    uint32_t idesc;
+    const float *wscale;   // [C][b_pad] sigma^2, or NULL (unscaled formats)
+    const float *wsig;
+    float *out;            // [B][C][T_o]
+    const float *acc_in;   // [B][C] partial sum of window 0 carried in, or NULL
+    float *acc_out;        // [B][C] partial sum of window T_o carried out, or NULL
+};
+
+// Launch-wide choices: tile width and the pipeline depths that follow.
+struct BatchCore {
+    int nt = 256, nsplit = 2, wpt = 4, t_int = 64, xst = 2, nacc = 2, smem = 0;
+    bool f8 = false;
+    int num_sms = 1;
+};
+
+// Checks that the plans can share one launch (tensor-core, CTN, one operand
+// format, one T_int, one device) and picks the tile width (tile_t = 0: the
+// widest that fits).  Sets the kernels' shared-memory attribute.
+bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t);
+
+// Fills one job.  x_mma: the voltages as the MMA reads them (the FP16
+// expansion for 8/4-bit integer inputs).  T_o, t_tiles and units follow from
+// T, t_shift and whether acc_out is given.
+bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, const void *x_mma, int T,
+                         float *out, int t_shift, const float *acc_in, float *acc_out);
+
+// Numbers the units of jobs[0..n) in order; returns the total.
+long long batch_index(BatchJob *jobs, int n);
+
+// One persistent launch over the table (already in device memory).
+cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
+                              unsigned *d_err, cudaStream_t s);
+
+}  // namespace bfi

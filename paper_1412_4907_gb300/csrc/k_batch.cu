@@ -1,60 +1,36 @@
 // Batched persistent tensor-core beamformer: the jobs of several plans
-// (sub-arrays, beam sets and channel counts of uneven sizes) in one launch.
+// (sub-arrays, beam sets and channel counts of uneven sizes, or chunks of
+// several streams) in one launch.
 //
 // Every job keeps its own plan (weights, per-beam scales) and its own input
-// and output buffers; the batch holds a device table with one entry per job
+// and output buffers; the launch reads a device table with one entry per job
 // (the two TMA tensor maps and the job's shape).  Work units are
-// (job, channel, time tile, M tile), M tile fastest so a voltage tile is
-// reused from L2 by consecutive MMAs; units are split among the persistent
-// CTAs by cost (K blocks per unit plus one for the epilogue), so jobs of very
-// different antenna counts balance.  Every job runs the streamed-weight
-// pipeline (one 64-column K block of weights and voltages per stage), so any
-// antenna count fits the same kernel; the epilogue and store warp are the
-// single-plan kernel's.  One launch per batch step; it can be captured in a
-// CUDA graph and replayed.
+// (job, channel, time tile, M tile), M tile fastest, numbered over all jobs;
+// CTA i takes units i, i + G, i + 2G, ... (G = grid size), so the CTAs that
+// run at the same moment work on neighbouring units of the same channel and
+// share its weight and voltage tiles through L2, and every CTA draws a
+// proportional share of every job (load balance without a cost model).
+// Every job runs the streamed pipeline (one 128-byte K block of weights and
+// voltages per stage), so any antenna count fits the same kernel; the
+// epilogue and store warp are the single-plan kernel's.  One launch per
+// batch step; it can be captured in a CUDA graph and replayed.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
+#include "batch.h"
 #include "tc_common.cuh"
 
 namespace bfi {
 
-struct __align__(128) BatchJob {
-    CUtensorMap xmap;   // voltages [C][T][2N]
-    CUtensorMap wmap;   // weight rows [C][M_pad][K_pad]
-    long long unit0;    // first global unit of the job
-    long long units;    // C x t_tiles x mt
-    long long cost0;    // total cost of the jobs before this one
-    int C, t_tiles, mt, kb, ke, w;   // w: cost of one unit
-    int T, T_o, B, b_pad;
-    uint32_t idesc;
-    const float *wscale;   // NULL for unscaled formats
-    const float *wsig;
-    float *out;
-};
-
 struct BatchArgs {
     const BatchJob *jobs;
     int n_jobs;
-    long long total_cost;
+    long long total_units;
     int nt, nsplit, wpt, t_int, xst, nacc;
     uint32_t stage_bytes;   // 16384 + nt * 128
     unsigned *err;
 };
-
-// First unit whose cost interval starts at or after `pos`.
-__device__ __forceinline__ long long unit_at(const BatchArgs &a, long long pos)
-{
-    int lo = 0, hi = a.n_jobs - 1;
-    while (lo < hi) {   // last job with cost0 <= pos
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.jobs[mid].cost0 <= pos) lo = mid;
-        else hi = mid - 1;
-    }
-    const BatchJob &J = a.jobs[lo];
-    const long long k = (pos - J.cost0 + J.w - 1) / J.w;
-    return J.unit0 + min(k, J.units);
-}
 
 __device__ __forceinline__ int job_of(const BatchArgs &a, long long u)
 {
@@ -71,21 +47,21 @@ struct UnitPos {
     int j, c, tt, m;
 };
 
-// Walks this CTA's units in order, tracking the job and decoding positions.
+// Walks this CTA's units (blockIdx.x, + gridDim.x, ...), tracking the job
+// and decoding positions.
 struct UnitWalk {
     const BatchArgs *a;
-    long long u, u1;
+    long long u;
     int j;
-    __device__ void begin(const BatchArgs &args, long long u0_, long long u1_)
+    __device__ void begin(const BatchArgs &args)
     {
         a = &args;
-        u = u0_;
-        u1 = u1_;
-        j = u < u1 ? job_of(args, u) : 0;
+        u = blockIdx.x;
+        j = u < args.total_units ? job_of(args, u) : 0;
     }
     __device__ bool next(UnitPos &p)
     {
-        if (u >= u1) return false;
+        if (u >= a->total_units) return false;
         while (u >= a->jobs[j].unit0 + a->jobs[j].units) ++j;
         const BatchJob &J = a->jobs[j];
         const int v = (int)(u - J.unit0);
@@ -94,7 +70,7 @@ struct UnitWalk {
         const int r = v / J.mt;
         p.tt = r % J.t_tiles;
         p.c = r / J.t_tiles;
-        ++u;
+        u += gridDim.x;
         return true;
     }
 };
@@ -145,16 +121,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    const long long u0 = unit_at(a, a.total_cost * blockIdx.x / gridDim.x);
-    const long long u1 = unit_at(a, a.total_cost * (blockIdx.x + 1) / gridDim.x);
-
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t cnt = 0, issued = 0;
             int st = 0, pj = -1;
             UnitWalk w;
-            w.begin(a, u0, u1);
+            w.begin(a);
             UnitPos p;
             bool ok = true;
             while (ok && w.next(p)) {
@@ -175,7 +148,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
                     const uint32_t dst = sx + st * a.stage_bytes;
                     mbar_arrive_expect_tx(b_full + 8 * st, bytes);
                     tma_load_3d(dst, &J.wmap, b_full + 8 * st, kb * J.ke, p.m * kRowsPerMTile, p.c);
-                    tma_load_3d(dst + 16384, &J.xmap, b_full + 8 * st, kb * J.ke, p.tt * a.nt, p.c);
+                    // window 0 starts t_shift samples before the chunk: those rows
+                    // (negative time coordinates) read as zeros
+                    tma_load_3d(dst + 16384, &J.xmap, b_full + 8 * st, kb * J.ke, p.tt * a.nt - J.t_shift, p.c);
                     if (++st == a.xst) st = 0;
                 }
             }
@@ -190,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
             uint32_t par = 0, tpar = 0;
             int st = 0, acc = 0;
             UnitWalk w;
-            w.begin(a, u0, u1);
+            w.begin(a);
             UnitPos p;
             bool ok = true;
             while (ok && w.next(p)) {
@@ -240,7 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         uint32_t tpar = 0, kt = 0;
         int acc = 0;
         UnitWalk w;
-        w.begin(a, u0, u1);
+        w.begin(a);
         UnitPos p;
         while (w.next(p)) {
             const BatchJob &J = a.jobs[p.j];
@@ -268,13 +243,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         // ------------------------------------------------------------ store warp
         uint32_t kt = 0;
         UnitWalk w;
-        w.begin(a, u0, u1);
+        w.begin(a);
         UnitPos p;
         while (w.next(p)) {
             const BatchJob &J = a.jobs[p.j];
             const uint32_t sb = kt % kStageDepth;
             if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
-            const TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, J.T, J.T_o, J.B, J.b_pad, J.C, J.wscale, J.wsig, J.out};
+            const TileOut o{a.nt,  a.nsplit, a.wpt, a.t_int,  J.T,      J.T_o,   J.B,
+                            J.b_pad, J.C,      J.wscale, J.wsig, J.out, J.acc_in, J.acc_out};
             store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), p.m * kBeamsPerMTile, p.c, p.tt, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
@@ -293,50 +269,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
 }  // namespace bfi
 
 // ----------------------------------------------------------------- host side
-using namespace bfi;
-
-struct bf_batch {
-    std::vector<bf_plan *> plans;
-    int n = 0;
-    int nt = 256, nsplit = 2, wpt = 4, t_int = 64, xst = 2, nacc = 2, smem = 0;
-    bool f8 = false;
-    int device = 0, num_sms = 0;
-    BatchJob *h_jobs = nullptr;   // pinned, so a captured copy reads it at replay
-    BatchJob *d_jobs = nullptr;
-    std::vector<void *> expand_buf;   // per job, FP16 copies of 8/4-bit inputs
-    std::vector<size_t> expand_bytes;
-    std::vector<const void *> in;
-    std::vector<int> n_samp;
-    std::vector<float *> out;
-    std::vector<char> set;
-    long long total_cost = 0, total_units = 0;
-    double flops = 0.0;
-    cudaStream_t last_stream = nullptr;
-    bool launched = false;   // a step was enqueued on last_stream
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    unsigned *d_err = nullptr;
-};
+namespace bfi {
 
 static int batch_stage_bytes(int nt) { return 16384 + nt * 128; }
 static int batch_layout_end(int xst, int nt)
 {
     return 1024 + xst * batch_stage_bytes(nt) + kStageDepth * kBeamsPerMTile * kMaxWinPerTile * 4 +
            8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth) + 8;
-}
-
-static void batch_free(bf_batch *b)
-{
-    if (!b) return;
-    if (b->launched) cudaStreamSynchronize(b->last_stream);
-    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->h_jobs) cudaFreeHost(b->h_jobs);
-    if (b->d_jobs) cudaFree(b->d_jobs);
-    if (b->d_err) cudaFree(b->d_err);
-    for (void *p : b->expand_buf)
-        if (p) cudaFree(p);
-    delete b;
 }
 
 // The attribute is a per-kernel maximum shared by every batch: it is set to
@@ -359,10 +298,10 @@ static int batch_win(int t_int)
     return (t_int == 64 || t_int == 32 || t_int == 16) ? t_int : (t_int % 16 == 0 ? 0 : -1);
 }
 
-#define BF_BATCH_DISPATCH(CALL)                                  \
+#define BF_BATCH_DISPATCH(CORE, CALL)                            \
     do {                                                         \
-        const int win_ = batch_win(b->t_int);                    \
-        if (b->f8) {                                             \
+        const int win_ = batch_win((CORE).t_int);                \
+        if ((CORE).f8) {                                         \
             switch (win_) {                                      \
             case 64: e = CALL(true, 64); break;                  \
             case 32: e = CALL(true, 32); break;                  \
@@ -382,44 +321,18 @@ static int batch_win(int t_int)
     } while (0)
 
 #define BF_ATTR(F, W) batch_attr<F, W>()
-#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, grid, b->smem, s)
+#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, grid, core.smem, s)
 
-static void batch_reindex(bf_batch *b)
+bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t)
 {
-    long long unit0 = 0, cost0 = 0;
-    double fl = 0.0;
-    for (int j = 0; j < b->n; ++j) {
-        BatchJob &J = b->h_jobs[j];
-        J.unit0 = unit0;
-        J.cost0 = cost0;
-        unit0 += J.units;
-        cost0 += J.units * J.w;
-        if (b->set[j]) {
-            const bf_plan *p = b->plans[j];
-            fl += 8.0 * p->N * p->B * p->C * (double)b->n_samp[j];
-        }
-    }
-    b->total_units = unit0;
-    b->total_cost = cost0;
-    b->flops = fl;
-}
-
-extern "C" {
-
-bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, int tile_t)
-{
-    if (!out) return set_error(BF_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!plans || n_plans < 1) return set_error(BF_ERR_ARG, "need at least one plan");
+    if (!plans || n < 1) return set_error(BF_ERR_ARG, "need at least one plan");
     const bf_plan *p0 = plans[0];
     if (!p0) return set_error(BF_ERR_ARG, "NULL plan");
-    for (int i = 0; i < n_plans; ++i) {
+    for (int i = 0; i < n; ++i) {
         const bf_plan *p = plans[i];
         if (!p) return set_error(BF_ERR_ARG, "NULL plan");
         if (p->wf.simt) return set_error(BF_ERR_UNSUPPORTED, "batches run tensor-core plans (not BF_C32)");
         if (p->layout != BF_LAYOUT_CTN) return set_error(BF_ERR_UNSUPPORTED, "batches take the CTN layout");
-        if (p->wf.op != p0->wf.op && (p->wf.op == kOpE4M3 || p0->wf.op == kOpE4M3))
-            return set_error(BF_ERR_UNSUPPORTED, "FP8 and 16-bit plans cannot share a batch");
         if (p->wf.op != p0->wf.op)
             return set_error(BF_ERR_UNSUPPORTED, "all plans of a batch must share the operand format");
         if (p->t_int != p0->t_int) return set_error(BF_ERR_UNSUPPORTED, "all plans of a batch must share T_int");
@@ -441,24 +354,159 @@ bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, in
         break;
     }
     if (!nt) return set_error(BF_ERR_UNSUPPORTED, "no tile width fits this T_int (and request)");
+    BatchCore c;
+    c.nt = nt;
+    c.t_int = t_int;
+    c.nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
+    c.wpt = nt / t_int;
+    c.nacc = std::min(kMaxAcc, kTmemCols / nt);
+    c.f8 = p0->wf.op == kOpE4M3;
+    c.num_sms = std::max(1, p0->num_sms);
+    const int fixed = batch_layout_end(0, nt);
+    c.xst = std::min(kMaxXStages, (kSmemLimit - fixed) / batch_stage_bytes(nt));
+    c.smem = std::max(batch_layout_end(c.xst, nt), 116 * 1024);
+    if (c.xst < 2 || batch_layout_end(c.xst, nt) > c.smem || c.smem > kSmemLimit)
+        return set_error(BF_ERR_UNSUPPORTED, "batch stages do not fit in shared memory");
+    cudaError_t e;
+    BF_BATCH_DISPATCH(c, BF_ATTR);
+    if (e != cudaSuccess) return cuda_error(e, "batch kernel attribute");
+    *core = c;
+    return BF_OK;
+}
+
+bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, const void *x_mma, int T,
+                         float *out, int t_shift, const float *acc_in, float *acc_out)
+{
+    if (T < 0) return set_error(BF_ERR_ARG, "n_samp must be >= 0");
+    if (t_shift < 0 || t_shift >= p->t_int) return set_error(BF_ERR_ARG, "carried samples must be in [0, T_int)");
+    const WeightFormat &f = p->wf;
+    memset((void *)J, 0, sizeof(BatchJob));
+    const int frame = t_shift + T;   // samples from the start of window 0
+    const int T_o = frame / p->t_int;
+    const int partial = (acc_out && frame % p->t_int) ? 1 : 0;
+    J->C = p->C;
+    J->t_tiles = ((T_o + partial) * p->t_int + core.nt - 1) / core.nt;
+    J->mt = f.m_pad / kRowsPerMTile;
+    J->kb = f.kb;
+    J->ke = f.ke;
+    J->T = T;
+    J->T_o = T_o;
+    J->B = p->B;
+    J->b_pad = f.b_pad;
+    J->t_shift = t_shift;
+    const uint32_t fmt = (f.op == kOpBF16) ? 1u : 0u;
+    J->idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(core.nt >> 3) << 17) |
+               ((uint32_t)(kRowsPerMTile >> 4) << 24);
+    J->wscale = f.qmax > 0.f ? p->d_wscale : nullptr;
+    J->wsig = p->d_wsig;
+    J->out = out;
+    J->acc_in = t_shift > 0 ? acc_in : nullptr;
+    J->acc_out = partial ? acc_out : nullptr;
+    J->units = (T_o + partial) > 0 ? (long long)J->C * J->t_tiles * J->mt : 0;
+    if (J->units > 0) {
+        if (T == 0) {   // nothing to read: the carried sum passes straight through
+            J->units = 0;
+            return set_error(BF_ERR_ARG, "a chunk with no samples cannot continue a window");
+        }
+        if (!encode_voltage_map(&J->xmap, x_mma, 2 * p->N, T, p->C, f.es, f.ke, core.nt))
+            return set_error(BF_ERR_ARG, "voltage tensor map rejected (pointer or row stride not 16-byte aligned?)");
+        if (!encode_weight_map(&J->wmap, p->d_w, f.k_pad, f.m_pad, p->C, f.es, f.ke))
+            return set_error(BF_ERR_CUDA, "weight tensor map rejected");
+    }
+    return BF_OK;
+}
+
+long long batch_index(BatchJob *jobs, int n)
+{
+    long long u = 0;
+    for (int j = 0; j < n; ++j) {
+        jobs[j].unit0 = u;
+        u += jobs[j].units;
+    }
+    return u;
+}
+
+cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
+                              unsigned *d_err, cudaStream_t s)
+{
+    if (total_units == 0) return cudaSuccess;
+    BatchArgs ka;
+    ka.jobs = d_jobs;
+    ka.n_jobs = n;
+    ka.total_units = total_units;
+    ka.nt = core.nt;
+    ka.nsplit = core.nsplit;
+    ka.wpt = core.wpt;
+    ka.t_int = core.t_int;
+    ka.xst = core.xst;
+    ka.nacc = core.nacc;
+    ka.stage_bytes = (uint32_t)batch_stage_bytes(core.nt);
+    ka.err = d_err;
+    const int grid = (int)std::min<long long>(core.num_sms, total_units);
+    cudaError_t e;
+    BF_BATCH_DISPATCH(core, BF_LAUNCH);
+    return e;
+}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+struct bf_batch {
+    std::vector<bf_plan *> plans;
+    int n = 0;
+    BatchCore core;
+    BatchJob *h_jobs = nullptr;   // pinned, so a captured copy reads it at replay
+    BatchJob *d_jobs = nullptr;
+    std::vector<void *> expand_buf;   // per job, FP16 copies of 8/4-bit inputs
+    std::vector<size_t> expand_bytes;
+    std::vector<const void *> in;
+    std::vector<int> n_samp;
+    std::vector<char> set;
+    long long total_units = 0;
+    double flops = 0.0;
+    cudaStream_t last_stream = nullptr;
+    bool launched = false;   // a step was enqueued on last_stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned *d_err = nullptr;
+};
+
+static void batch_free(bf_batch *b)
+{
+    if (!b) return;
+    if (b->launched) cudaStreamSynchronize(b->last_stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_err) cudaFree(b->d_err);
+    for (void *p : b->expand_buf)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+static void drop_graph(bf_batch *b)
+{
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+}
+
+extern "C" {
+
+bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, int tile_t)
+{
+    if (!out) return set_error(BF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    BatchCore core;
+    bf_status st = batch_core_init(&core, plans, n_plans, tile_t);
+    if (st != BF_OK) return st;
     bf_batch *b = new bf_batch();
     b->plans.assign(plans, plans + n_plans);
     b->n = n_plans;
-    b->nt = nt;
-    b->t_int = t_int;
-    b->nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
-    b->wpt = nt / t_int;
-    b->nacc = std::min(kMaxAcc, kTmemCols / nt);
-    b->f8 = p0->wf.op == kOpE4M3;
-    b->device = p0->device;
-    b->num_sms = p0->num_sms;
-    const int fixed = batch_layout_end(0, nt);
-    b->xst = std::min(kMaxXStages, (kSmemLimit - fixed) / batch_stage_bytes(nt));
-    b->smem = std::max(batch_layout_end(b->xst, nt), 116 * 1024);
-    if (b->xst < 2 || batch_layout_end(b->xst, nt) > b->smem || b->smem > kSmemLimit) {
-        batch_free(b);
-        return set_error(BF_ERR_UNSUPPORTED, "batch stages do not fit in shared memory");
-    }
+    b->core = core;
     cudaError_t e;
     if ((e = cudaHostAlloc((void **)&b->h_jobs, sizeof(BatchJob) * n_plans, cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_jobs, sizeof(BatchJob) * n_plans)) != cudaSuccess ||
@@ -468,18 +516,11 @@ bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, in
         return cuda_error(e, "batch allocation");
     }
     memset((void *)b->h_jobs, 0, sizeof(BatchJob) * n_plans);
-    for (int j = 0; j < n_plans; ++j) b->h_jobs[j].w = 1;
     b->expand_buf.assign(n_plans, nullptr);
     b->expand_bytes.assign(n_plans, 0);
     b->in.assign(n_plans, nullptr);
     b->n_samp.assign(n_plans, 0);
-    b->out.assign(n_plans, nullptr);
     b->set.assign(n_plans, 0);
-    BF_BATCH_DISPATCH(BF_ATTR);
-    if (e != cudaSuccess) {
-        batch_free(b);
-        return cuda_error(e, "batch kernel attribute");
-    }
     *out = b;
     return BF_OK;
 }
@@ -498,13 +539,7 @@ bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
         cudaError_t e = cudaStreamSynchronize(b->last_stream);   // the table may be read by a copy in flight
         if (e != cudaSuccess) return cuda_error(e, "batch synchronize");
     }
-    if (b->graph_exec) {   // a captured step refers to the old inputs
-        cudaGraphExecDestroy(b->graph_exec);
-        cudaGraphDestroy(b->graph);
-        b->graph_exec = nullptr;
-        b->graph = nullptr;
-    }
-    const WeightFormat &f = p->wf;
+    drop_graph(b);   // a captured step refers to the old inputs
     const void *xin = x;
     const bool expand = p->dtype == BF_CI8 || p->dtype == BF_CI4;
     if (expand && T_o > 0) {
@@ -519,35 +554,21 @@ bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
         }
         xin = b->expand_buf[job];
     }
-    BatchJob &J = b->h_jobs[job];
-    J.C = p->C;
-    J.t_tiles = (T_o * p->t_int + b->nt - 1) / b->nt;   // whole windows only
-    J.mt = f.m_pad / kRowsPerMTile;
-    J.kb = f.kb;
-    J.ke = f.ke;
-    J.w = f.kb + 1;
-    J.T = T;
-    J.T_o = T_o;
-    J.B = p->B;
-    J.b_pad = f.b_pad;
-    const uint32_t fmt = (f.op == kOpBF16) ? 1u : 0u;
-    J.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(b->nt >> 3) << 17) |
-              ((uint32_t)(kRowsPerMTile >> 4) << 24);
-    J.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;
-    J.wsig = p->d_wsig;
-    J.out = out;
-    J.units = T_o > 0 ? (long long)J.C * J.t_tiles * J.mt : 0;
-    if (J.units > 0) {
-        if (!encode_voltage_map(&J.xmap, xin, 2 * p->N, T, p->C, f.es, f.ke, b->nt))
-            return set_error(BF_ERR_ARG, "voltage tensor map rejected (pointer or row stride not 16-byte aligned?)");
-        if (!encode_weight_map(&J.wmap, p->d_w, f.k_pad, f.m_pad, p->C, f.es, f.ke))
-            return set_error(BF_ERR_CUDA, "weight tensor map rejected");
-    }
+    BatchJob J;
+    bf_status st = batch_fill_job(b->core, &J, p, xin, T, out, 0, nullptr, nullptr);
+    if (st != BF_OK) return st;
+    b->h_jobs[job] = J;
     b->in[job] = x;
     b->n_samp[job] = T;
-    b->out[job] = out;
     b->set[job] = 1;
-    batch_reindex(b);
+    b->total_units = batch_index(b->h_jobs, b->n);
+    double fl = 0.0;
+    for (int j = 0; j < b->n; ++j)
+        if (b->set[j]) {
+            const bf_plan *q = b->plans[j];
+            fl += 8.0 * q->N * q->B * q->C * (double)b->n_samp[j];
+        }
+    b->flops = fl;
     return BF_OK;
 }
 
@@ -571,20 +592,7 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
     }
     e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * b->n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_error(e, "batch table upload");
-    BatchArgs ka;
-    ka.jobs = b->d_jobs;
-    ka.n_jobs = b->n;
-    ka.total_cost = b->total_cost;
-    ka.nt = b->nt;
-    ka.nsplit = b->nsplit;
-    ka.wpt = b->wpt;
-    ka.t_int = b->t_int;
-    ka.xst = b->xst;
-    ka.nacc = b->nacc;
-    ka.stage_bytes = (uint32_t)batch_stage_bytes(b->nt);
-    ka.err = b->d_err;
-    const int grid = (int)std::min<long long>(b->num_sms, b->total_units);
-    BF_BATCH_DISPATCH(BF_LAUNCH);
+    e = batch_core_launch(b->core, b->d_jobs, b->n, b->total_units, b->d_err, s);
     if (e != cudaSuccess) return cuda_error(e, "batched tensor-core kernel");
     return BF_OK;
 }
@@ -594,15 +602,12 @@ bf_status bf_batch_capture(bf_batch *b, void *stream)
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     if (!stream) return set_error(BF_ERR_ARG, "capture needs a non-default stream");
     cudaStream_t s = (cudaStream_t)stream;
-    if (b->graph_exec) {
-        cudaGraphExecDestroy(b->graph_exec);
-        cudaGraphDestroy(b->graph);
-        b->graph_exec = nullptr;
-        b->graph = nullptr;
-    }
+    drop_graph(b);
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_error(e, "begin capture");
+    const bool was = b->launched;
     bf_status st = bf_batch_execute(b, stream);
+    b->launched = was;   // nothing ran yet
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     if (st != BF_OK) {
@@ -648,7 +653,7 @@ bf_status bf_batch_sync(bf_batch *b)
 bf_status bf_batch_query(const bf_batch *b, int *tile_t, long long *units, double *flops)
 {
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
-    if (tile_t) *tile_t = b->nt;
+    if (tile_t) *tile_t = b->core.nt;
     if (units) *units = b->total_units;
     if (flops) *flops = b->flops;
     return BF_OK;

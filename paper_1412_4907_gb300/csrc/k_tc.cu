@@ -56,6 +56,8 @@ struct TcKernelArgs {
     const float *wscale;   // [C][b_pad] sigma^2
     const float *wsig;     // [C][b_pad] sigma
     float *out;
+    const float *acc_in;   // always NULL here (no carried window)
+    float *acc_out;        // always NULL here
     unsigned *err;
 };
 
@@ -342,7 +344,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int cols = a.nt / a.nsplit;
         const int col0 = h * cols;
         const bool active = h < a.nsplit;
-        const TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, a.T, a.T_o, a.B, a.b_pad, a.c_total, a.wscale, a.wsig, a.out};
         uint32_t tpar = 0, kt = 0;
         int acc = 0;
         bool ok = true;
@@ -374,12 +375,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
                     const uint32_t tempty = b_tempty + 8 * acc;
                     if (COMPLEX) {
-                        if (active) epi_complex_tile(o, taddr, cols, col0, tt, lane, b, bvalid, cg);
+                        if (active) epi_complex_tile(a, taddr, cols, col0, tt, lane, b, bvalid, cg);
                         tile_release(tempty, lane);
                     } else if (!active) {
                         tile_release(tempty, lane);
                     } else {
-                        epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, bvalid, cg,
+                        epi_power_tile<WIN>(a, taddr, cols, h, lane, bq, b, bvalid, cg,
                                             stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
                     }
                     if (++acc == a.nacc) acc = 0;
@@ -393,7 +394,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (warp == kStoreWarp && !COMPLEX) {
         // ------------------------------------------------------------ store warp
         // writes each staged tile as one run of windows per beam
-        const TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, a.T, a.T_o, a.B, a.b_pad, a.c_total, a.wscale, a.wsig, a.out};
         uint32_t kt = 0;
         bool ok = true;
         for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         ok = false;
                         break;
                     }
-                    store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), (m0 + s) * kBeamsPerMTile, cg, tt,
+                    store_tile(a, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), (m0 + s) * kBeamsPerMTile, cg, tt,
                                lane);
                     __syncwarp();
                     if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
@@ -648,6 +648,8 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
+    ka.acc_in = nullptr;
+    ka.acc_out = nullptr;
     ka.err = p->d_err;
     if (ka.ct_total == 0) return cudaSuccess;
     if (!layout_ok(cfg, f.kb) || ka.gmax != (cfg.stream ? 0 : cfg.group)) {   // final guard before launch

@@ -54,12 +54,17 @@ __device__ __forceinline__ float sumsq_pk(const uint32_t *r)
 }
 
 // What the epilogue and the store warp need to know about the output of the
-// plan (or batched job) a tile belongs to.
+// plan (or batched job) a tile belongs to.  The tile functions below are
+// templates over the description type, so the single-plan kernel passes its
+// kernel parameters directly (read from the parameter space, not copied into
+// registers) and the batched kernel passes a TileOut built from its job entry.
 struct TileOut {
     int nt, nsplit, wpt, t_int, T, T_o, B, b_pad, c_total;
     const float *wscale;   // [C][b_pad] sigma^2, or NULL (unscaled)
     const float *wsig;     // [C][b_pad] sigma
     float *out;            // powers [B][C][T_o] or beams [B][C][T][2]
+    const float *acc_in = nullptr;   // [B][C] partial sum added to window 0 (carried in)
+    float *acc_out = nullptr;        // [B][C] receives window T_o, left open (carried out)
 };
 
 // Hand a TMEM accumulator back to the MMA issuer (after its loads completed).
@@ -76,8 +81,8 @@ __device__ __forceinline__ void tile_release(uint32_t b_tempty_acc, int lane)
 // shuffle, scale, and stage the window powers for the store warp.
 // WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
 // -1 = any T_int (per-column window counter).
-template <int WIN>
-__device__ __forceinline__ void epi_power_tile(const TileOut &o, uint32_t taddr, int cols, int h, int lane, int bq,
+template <int WIN, class O>
+__device__ __forceinline__ void epi_power_tile(const O &o, uint32_t taddr, int cols, int h, int lane, int bq,
                                                int b, bool bvalid, int cg, float *stg, uint32_t b_tempty_acc,
                                                uint32_t b_sfull_sb)
 {
@@ -152,7 +157,8 @@ __device__ __forceinline__ void epi_power_tile(const TileOut &o, uint32_t taddr,
 }
 
 // Complex-beam epilogue of one warp for one tile: beams straight to HBM.
-__device__ __forceinline__ void epi_complex_tile(const TileOut &o, uint32_t taddr, int cols, int col0, int tt,
+template <class O>
+__device__ __forceinline__ void epi_complex_tile(const O &o, uint32_t taddr, int cols, int col0, int tt,
                                                  int lane, int b, bool bvalid, int cg)
 {
     const int part = (lane >> 4) & 1;
@@ -180,10 +186,28 @@ __device__ __forceinline__ void epi_complex_tile(const TileOut &o, uint32_t tadd
 }
 
 // The store warp's write of one staged tile: one run of windows per beam.
-__device__ __forceinline__ void store_tile(const TileOut &o, const float *stg, int b_tile0, int cg, int tt, int lane)
+// With a carried integration, window 0 first takes the partial sum that the
+// previous chunk left, and window T_o (open at the end of this chunk) goes to
+// acc_out instead of the output.
+template <class O>
+__device__ __forceinline__ void store_tile(const O &o, float *stg, int b_tile0, int cg, int tt, int lane)
 {
-    const bool vec = (o.T_o & 3) == 0 && (o.wpt & 3) == 0;
     const int j0 = tt * o.wpt;
+    if (o.acc_in && j0 == 0) {
+        for (int bl = lane; bl < kBeamsPerMTile; bl += 32) {
+            const int bb = b_tile0 + bl;
+            if (bb < o.B) stg[bl * kMaxWinPerTile] += o.acc_in[(size_t)bb * o.c_total + cg];
+        }
+        __syncwarp();
+    }
+    if (o.acc_out && o.T_o >= j0 && o.T_o < j0 + o.wpt) {
+        const int k = o.T_o - j0;
+        for (int bl = lane; bl < kBeamsPerMTile; bl += 32) {
+            const int bb = b_tile0 + bl;
+            if (bb < o.B) o.acc_out[(size_t)bb * o.c_total + cg] = stg[bl * kMaxWinPerTile + k];
+        }
+    }
+    const bool vec = (o.T_o & 3) == 0 && (o.wpt & 3) == 0;
     const int nj = min(o.wpt, o.T_o - j0);
     if (vec && o.wpt == 4) {
         // one float4 per beam: lanes take beams lane and lane + 32

@@ -108,3 +108,65 @@ def apply_cached(plan, n_samp: int, cache: str | None = DEFAULT_CACHE) -> bool:
         return False
     bf_plan_set_tiles(plan.handle, cfg["tile_t"], cfg["group_tiles"], cfg["x_stages"])
     return True
+
+
+# ------------------------------------------------------------ batched launch
+def batch_key(plans, n_samps) -> str:
+    """Cache key of a batch: T_int, operand dtype and the sorted job shapes."""
+    shapes = sorted((p.N, p.B, p.C, int(t)) for p, t in zip(plans, n_samps))
+    h = hash(tuple(shapes)) & 0xFFFFFFFF
+    return f"batch_Ti{plans[0].t_int}_d{plans[0].dtype}_n{len(plans)}_{h:08x}"
+
+
+def batch_candidates(t_int: int):
+    unit = 16 * t_int // math.gcd(16, t_int)
+    return [t for t in range(256, unit - 1, -16) if t % unit == 0 and t // t_int <= 16]
+
+
+def time_batch(batch, reps: int = 5) -> float:
+    """Mean milliseconds of one graph replay of a bound, captured batch."""
+    import torch
+    s = batch.stream
+    for _ in range(2):
+        batch.replay()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        batch.replay()
+    b.record(s)
+    b.synchronize()
+    batch.sync()
+    return a.elapsed_time(b) / reps
+
+
+def tune_batch(plans, xs, outs, n_samps=None, stream=None, reps: int = 5, cache: str | None = DEFAULT_CACHE,
+               verbose: bool = False) -> dict:
+    """Time the batched launch of ``plans`` on inputs ``xs`` (outputs ``outs``)
+    for every feasible tile width, and return {"tile_t", "ms", "table"}; the
+    choice is cached under the batch's shape key."""
+    from . import Batch
+    if n_samps is None:
+        n_samps = [p.n_samp(x) for p, x in zip(plans, xs)]
+    table = []
+    for t in batch_candidates(plans[0].t_int):
+        try:
+            batch = Batch(plans, tile_t=t, stream=stream)
+        except BFError:
+            continue
+        for j, (x, o, T) in enumerate(zip(xs, outs, n_samps)):
+            batch.set(j, x, o, n_samp=T)
+        batch.capture()
+        ms = time_batch(batch, reps)
+        batch.close()
+        table.append({"tile_t": t, "ms": ms})
+        if verbose:
+            print(f"batch tile_t={t:3d}: {ms:.3f} ms", flush=True)
+    best = min(table, key=lambda r: r["ms"])
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        data = json.load(open(cache)) if os.path.exists(cache) else {}
+        data[batch_key(plans, n_samps)] = {"tile_t": best["tile_t"]}
+        tmp = cache + f".tmp{os.getpid()}"
+        json.dump(data, open(tmp, "w"), indent=1)
+        os.replace(tmp, cache)
+    return {"tile_t": best["tile_t"], "ms": best["ms"], "table": table}

@@ -23,7 +23,7 @@ def bf():
 
 def declared():
     hdr = open(HEADER).read()
-    return set(re.findall(r"^(?:bf_status|const char \*)\s*(bf_\w+)\(", hdr, re.M))
+    return set(re.findall(r"^(?:bf_status|const char \*|double)\s*(bf_\w+)\(", hdr, re.M))
 
 
 def test_every_declared_symbol_is_exported(bf):
@@ -88,6 +88,16 @@ def test_null_and_bad_handles(bf):
     assert lib.bf_batch_sync(None) == bf.BF_ERR_ARG
     assert lib.bf_batch_query(None, None, None, None) == bf.BF_ERR_ARG
     assert lib.bf_batch_destroy(None) == bf.BF_OK
+    assert lib.bf_server_create(ctypes.byref(b), None, 1, 1 << 20, 2, 0) == bf.BF_ERR_ARG
+    assert lib.bf_server_create(ctypes.byref(b), None, 1, 1 << 20, 0, 0) == bf.BF_ERR_ARG
+    assert lib.bf_server_submit(None, 0, None, 1, None, None) == bf.BF_ERR_ARG
+    n = ctypes.c_int()
+    assert lib.bf_server_poll(None, None, 0, ctypes.byref(n), 0) == bf.BF_ERR_ARG
+    assert lib.bf_server_drain(None, 0) == bf.BF_ERR_ARG
+    assert lib.bf_server_pause(None, 1) == bf.BF_ERR_ARG
+    assert lib.bf_server_stats(None, None) == bf.BF_ERR_ARG
+    assert lib.bf_server_destroy(None) == bf.BF_OK
+    assert lib.bf_server_now() > 0.0
     out = ctypes.c_void_p(123)
     assert lib.bf_plan_create(ctypes.byref(out), 0, None, None, 0, None, 0, None, 0, 0, 0, None) == bf.BF_ERR_ARG
     assert out.value is None
