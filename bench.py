@@ -60,7 +60,7 @@ def peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("k_tc.cu", "tc_common.cuh", "ptx.cuh", "bf_internal.h"):
+    for f in ("k_tc.cu", "ptx.cuh", "bf_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1412_4907_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -468,7 +468,8 @@ def run_batched(args):
     import paper_1412_4907_gb300 as bf
     from paper_1412_4907_gb300 import tune
     torch.cuda.set_device(0)
-    jobs = synth.config4_jobs()
+    div = max(1, args.batched_chan_div)
+    jobs = synth.config4_jobs(chan_choices=(128 // div, 512 // div, 2048 // div))
     stream = torch.cuda.Stream()
     plans, outs, n_samps = [], [], []
     F = 0.0
@@ -504,7 +505,8 @@ def run_batched(args):
              "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                           "peak_source": f"bf16_tflops_sustained {pk_kind}"},
              "config": {"workload": "48 sub-array jobs: N in {16,32,64,128,256} of the 256-antenna 200 m layout, "
-                                    "B log-uniform 8..4096, C in {128,512,2048}, T 4096 FP16, T_int 64",
+                                    "B log-uniform 8..4096, C in {128,512,2048}" + (f" / {div}" if div > 1 else "")
+                                    + ", T 4096 FP16, T_int 64",
                         "total_tflop": F / 1e12, "jobs": len(jobs),
                         "l2": "no flush: 74 GB of voltages and 21 GB of weights per step exceed the 129 MB L2"}}
         d.update(extra)
@@ -665,6 +667,8 @@ def run_serve(args):
         F += flops(N, B, C, T)
         h2d += C * T * N * (4 if mode == synth.C16F else 2)
     kernel_ms = st["kernel_ms"] - base["kernel_ms"]
+    copy_ms = st["copy_in_ms"] - base["copy_in_ms"]
+    copy_b = st["copy_in_bytes"] - base["copy_in_bytes"]
     steps = st["steps"] - base["steps"]
     sustained = F / (t_last - t0) / 1e12
     pk, pk_kind = peaks()
@@ -681,6 +685,8 @@ def run_serve(args):
                         "unit": "TFLOP/s", "frac": F / (kernel_ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"],
                         "peak_source": f"bf16_tflops_sustained {pk_kind}"},
            "h2d_gbps_offered": h2d / args.serve_seconds / 1e9, "h2d_gbps_achieved": h2d / (t_last - t0) / 1e9,
+           "h2d_gbps_while_copying": copy_b / (copy_ms * 1e-3) / 1e9 if copy_ms else None,
+           "copy_in_busy_frac": copy_ms * 1e-3 / (t_last - t0),
            "steps": steps, "mean_chunks_per_step": len(ids) / max(1, steps), "max_chunks_per_step": st["max_jobs_per_step"],
            "arena_gb": st["arena_bytes"] / 2**30, "arena_peak_gb": st["arena_peak"] / 2**30,
            "submit_lag_s": t_sub_end - (t0 + arrivals[-1][0]) if arrivals else 0.0,
@@ -738,6 +744,8 @@ def main():
                     help="precision sweep on the config-3 shape (one JSON line per mode) instead of the benchmark")
     ap.add_argument("--batched", action="store_true",
                     help="batched uneven launch of 48 sub-array jobs (one JSON line per variant)")
+    ap.add_argument("--batched-chan-div", type=int, default=1,
+                    help="divide every job's channel count (smaller case of the same jobs, for profiling)")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream of 6 configurations with Poisson arrivals (p50/p99 latency)")
     ap.add_argument("--serve-rate", type=float, default=400.0, help="chunk arrivals per second")

@@ -361,6 +361,8 @@ typedef struct bf_server_counters {
     int tile_t;
     double flops;        /* 8 N B C T summed over completed chunks */
     double kernel_ms;    /* device time of the batched launches (CUDA events) */
+    double copy_in_ms;   /* span of each step's host-to-device chunk copies, summed */
+    double copy_in_bytes;
     size_t arena_bytes, arena_peak;
 } bf_server_counters;
 

@@ -42,7 +42,8 @@ class bf_completion(ctypes.Structure):
 class bf_server_counters(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("steps", ctypes.c_longlong),
                 ("max_jobs_per_step", ctypes.c_int), ("tile_t", ctypes.c_int), ("flops", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double), ("arena_bytes", ctypes.c_size_t), ("arena_peak", ctypes.c_size_t)]
+                ("kernel_ms", ctypes.c_double), ("copy_in_ms", ctypes.c_double), ("copy_in_bytes", ctypes.c_double),
+                ("arena_bytes", ctypes.c_size_t), ("arena_peak", ctypes.c_size_t)]
 
 SIGNATURES = {
     "bf_plan_create": [ctypes.POINTER(_P), _I, _P, _P, _I, _P, _I, _P, _I, _I, _I, _P],

@@ -116,11 +116,10 @@ struct Slot {
     BatchJob *d_jobs = nullptr;
     unsigned *d_err = nullptr;
     unsigned *h_err = nullptr;    // pinned
-    cudaEvent_t ev_in = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+    cudaEvent_t ev_h0 = nullptr, ev_in = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
     std::vector<Request *> reqs;
-    bool busy = false, done = false, timed = false;
-    double flops = 0.0;
-    int index = 0;
+    bool busy = false, done = false;
+    size_t in_bytes = 0;
     bf_server *owner = nullptr;
 };
 
@@ -145,7 +144,8 @@ struct bf_server {
     std::deque<Request *> completed;
     long long next_id = 1, submitted = 0, n_completed = 0, steps = 0;
     int inflight = 0, max_jobs = 0;
-    double flops_done = 0.0, kernel_ms = 0.0;
+    double flops_done = 0.0, kernel_ms = 0.0, copy_in_ms = 0.0;
+    double copy_in_bytes = 0.0;
     bool stop = false;
     bool paused = false;                // admit nothing (chunks queue)
     std::string fault;                  // first CUDA error the scheduler met
@@ -224,8 +224,12 @@ static std::string launch_step(bf_server *s, Slot &sl)
 {
     cudaError_t e;
     const double t0 = now_s();
+    if ((e = cudaEventRecord(sl.ev_h0, s->s_in)) != cudaSuccess)
+        return std::string("step ordering: ") + cudaGetErrorString(e);
+    sl.in_bytes = 0;
     for (Request *r : sl.reqs) {
         r->t_start = t0;
+        sl.in_bytes += r->in_bytes;
         if (r->in_bytes) {
             e = cudaMemcpyAsync(s->arena_base + r->off, r->hx, r->in_bytes, cudaMemcpyHostToDevice, s->s_in);
             if (e != cudaSuccess) return std::string("chunk copy: ") + cudaGetErrorString(e);
@@ -236,7 +240,6 @@ static std::string launch_step(bf_server *s, Slot &sl)
         (e = cudaMemsetAsync(sl.d_err, 0, sizeof(unsigned), s->s_k)) != cudaSuccess)
         return std::string("step ordering: ") + cudaGetErrorString(e);
     int n = 0;
-    sl.flops = 0.0;
     for (Request *r : sl.reqs) {
         Stream &st = s->streams[r->cfg];
         bf_plan *p = st.plan;
@@ -254,7 +257,6 @@ static std::string launch_step(bf_server *s, Slot &sl)
         if (bs != BF_OK) return std::string("job setup: ") + bf_last_error();
         if (rem) st.cur = 1 - st.cur;
         st.carry = rem;
-        sl.flops += 8.0 * p->N * p->B * p->C * (double)r->T;
         ++n;
     }
     const long long units = batch_index(sl.h_jobs, n);
@@ -299,11 +301,16 @@ static void scheduler(bf_server *s)
         // retire finished steps: kernel time from the events
         for (Slot &sl : s->slots) {
             if (!sl.busy || !sl.done) continue;
-            float ms = 0.f;
+            float ms = 0.f, ms_in = 0.f;
             lock.unlock();
             const cudaError_t e = cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k1);
+            const cudaError_t e2 = cudaEventElapsedTime(&ms_in, sl.ev_h0, sl.ev_in);
             lock.lock();
             if (e == cudaSuccess) s->kernel_ms += ms;
+            if (e2 == cudaSuccess) {
+                s->copy_in_ms += ms_in;
+                s->copy_in_bytes += (double)sl.in_bytes;
+            }
             sl.busy = sl.done = false;
             sl.reqs.clear();
             --s->inflight;
@@ -377,6 +384,7 @@ static void server_free(bf_server *s)
         if (sl.d_jobs) cudaFree(sl.d_jobs);
         if (sl.d_err) cudaFree(sl.d_err);
         if (sl.h_err) cudaFreeHost(sl.h_err);
+        if (sl.ev_h0) cudaEventDestroy(sl.ev_h0);
         if (sl.ev_in) cudaEventDestroy(sl.ev_in);
         if (sl.ev_k0) cudaEventDestroy(sl.ev_k0);
         if (sl.ev_k1) cudaEventDestroy(sl.ev_k1);
@@ -434,14 +442,13 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
     s->slots.resize(max_steps);
     for (int i = 0; i < max_steps && e == cudaSuccess; ++i) {
         Slot &sl = s->slots[i];
-        sl.index = i;
         sl.owner = s;
         if ((e = cudaHostAlloc((void **)&sl.h_jobs, sizeof(BatchJob) * n_configs, cudaHostAllocDefault)) ==
                 cudaSuccess &&
             (e = cudaMalloc((void **)&sl.d_jobs, sizeof(BatchJob) * n_configs)) == cudaSuccess &&
             (e = cudaMalloc((void **)&sl.d_err, sizeof(unsigned))) == cudaSuccess &&
             (e = cudaHostAlloc((void **)&sl.h_err, sizeof(unsigned), cudaHostAllocDefault)) == cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventCreate(&sl.ev_h0)) == cudaSuccess && (e = cudaEventCreate(&sl.ev_in)) == cudaSuccess &&
             (e = cudaEventCreate(&sl.ev_k0)) == cudaSuccess)
             e = cudaEventCreate(&sl.ev_k1);
         if (e == cudaSuccess) *sl.h_err = 0;
@@ -552,6 +559,8 @@ bf_status bf_server_stats(bf_server *s, bf_server_counters *out)
     out->max_jobs_per_step = s->max_jobs;
     out->flops = s->flops_done;
     out->kernel_ms = s->kernel_ms;
+    out->copy_in_ms = s->copy_in_ms;
+    out->copy_in_bytes = s->copy_in_bytes;
     out->arena_bytes = s->arena_bytes;
     out->arena_peak = s->arena.peak();
     out->tile_t = s->core.nt;

@@ -37,12 +37,26 @@
 // Every wait is bounded (2 s); a timeout raises the plan's error word, all
 // roles leave their loops, in-flight copies and MMAs are drained and TMEM is
 // freed before the CTA exits.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 
-#include "tc_common.cuh"
+#include "bf_internal.h"
+#include "ptx.cuh"
+#include "tmap.h"
 
 namespace bfi {
+
+constexpr int kEpiWarps = 8;
+constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
+constexpr int kTcThreads = (3 + kEpiWarps) * 32;
+constexpr int kStageDepth = 4;                     // staged tiles in flight
+constexpr int kTmemCols = 512;
+constexpr int kMaxWinPerTile = 16;
+constexpr int kMaxXStages = 8;
+constexpr int kMaxAcc = 8;                         // TMEM accumulators (512 columns / tile)
+constexpr uint64_t kWaitLimitCycles = 4000000000ull;   // SM cycles: about 2 s at the maximum clock
 
 struct TcKernelArgs {
     long long ct_total;                 // channels x time tiles
@@ -56,8 +70,6 @@ struct TcKernelArgs {
     const float *wscale;   // [C][b_pad] sigma^2
     const float *wsig;     // [C][b_pad] sigma
     float *out;
-    const float *acc_in;   // always NULL here (no carried window)
-    float *acc_out;        // always NULL here
     unsigned *err;
 };
 
@@ -70,6 +82,57 @@ __device__ __forceinline__ void group_tiles(const TcKernelArgs &a, int g, int &m
         gs = a.g_base;
         m0 = a.g_rem * (a.g_base + 1) + (g - a.g_rem) * a.g_base;
     }
+}
+
+// Bounded wait that ignores the abort flag (used only to drain on abort).
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 400000000ll) break;   // ~0.2 s
+}
+
+// Sum of squares of 16 values with four independent chains.
+__device__ __forceinline__ float sumsq16(const float *v)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+        s0 = fmaf(v[i], v[i], s0);
+        s1 = fmaf(v[i + 1], v[i + 1], s1);
+        s2 = fmaf(v[i + 2], v[i + 2], s2);
+        s3 = fmaf(v[i + 3], v[i + 3], s3);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+__device__ __forceinline__ float sumsq32(const float *v)
+{
+    return sumsq16(v) + sumsq16(v + 16);
+}
+
+// Sum of squares of 64 values with eight independent chains.
+__device__ __forceinline__ float sumsq64(const float *v)
+{
+    float s[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 64; i += 8)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = fmaf(v[i + j], v[i + j], s[j]);
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+// Sum of squares of n (multiple of 8) raw FP32 values with packed FMAs in
+// four independent chains, combined in a fixed order.
+template <int n>
+__device__ __forceinline__ float sumsq_pk(const uint32_t *r)
+{
+    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) sq_acc2(acc[i & 3], r[2 * i], r[2 * i + 1]);
+    return (sum2(acc[0]) + sum2(acc[1])) + (sum2(acc[2]) + sum2(acc[3]));
 }
 
 // WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
@@ -340,10 +403,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int e = warp - 2;
         const int q = warp & 3;               // TMEM lane quarter this warp may access
         const int h = e >> 2;                 // column slice
+        const int part = (lane >> 4) & 1;     // 0: re row, 1: im row
         const int bq = q * 16 + (lane & 15);  // beam within the M tile
         const int cols = a.nt / a.nsplit;
         const int col0 = h * cols;
         const bool active = h < a.nsplit;
+        const int wps = COMPLEX ? 0 : cols / a.t_int;   // windows per slice
         uint32_t tpar = 0, kt = 0;
         int acc = 0;
         bool ok = true;
@@ -373,15 +438,107 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int b = (m0 + s) * kBeamsPerMTile + bq;
                     const bool bvalid = b < a.B;
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
-                    const uint32_t tempty = b_tempty + 8 * acc;
+                    // hand the accumulator back to the MMA as soon as it has been read
+                    auto release = [&]() {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_relaxed(b_tempty + 8 * acc);
+                    };
                     if (COMPLEX) {
-                        if (active) epi_complex_tile(a, taddr, cols, col0, tt, lane, b, bvalid, cg);
-                        tile_release(tempty, lane);
+                        if (active) {
+                            const float sg = bvalid ? a.wsig[(size_t)cg * a.b_pad + b] : 0.f;
+                            float2 *o2 = reinterpret_cast<float2 *>(a.out);
+                            const size_t ob = ((size_t)b * a.c_total + cg) * a.T;
+                            for (int ch = 0; ch < cols / 16; ++ch) {
+                                float v[16], o[16];
+                                tmem_ld16(taddr + ch * 16, v);
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 16);
+                                const int t0 = tt * a.nt + col0 + ch * 16;
+                                // lanes 0-15 hold the re row and store samples 0-7 of the
+                                // chunk; lanes 16-31 hold the im row and store samples 8-15
+                                if (bvalid && part == 0) {
+#pragma unroll
+                                    for (int i = 0; i < 8; ++i)
+                                        if (t0 + i < a.T) o2[ob + t0 + i] = make_float2(v[i] * sg, o[i] * sg);
+                                } else if (bvalid) {
+#pragma unroll
+                                    for (int i = 8; i < 16; ++i)
+                                        if (t0 + i < a.T) o2[ob + t0 + i] = make_float2(o[i] * sg, v[i] * sg);
+                                }
+                            }
+                        }
+                        release();
                     } else if (!active) {
-                        tile_release(tempty, lane);
+                        release();
                     } else {
-                        epi_power_tile<WIN>(a, taddr, cols, h, lane, bq, b, bvalid, cg,
-                                            stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
+                        const float scale = bvalid ? (a.wscale ? a.wscale[(size_t)cg * a.b_pad + b] : 1.f) : 0.f;
+                        float *stg = stage + sb * (kBeamsPerMTile * kMaxWinPerTile);
+                        float ws = 0.f;
+                        int wi = 0, cnt = 0;
+                        auto emit = [&](float sum) {
+                            const float pw = (sum + __shfl_xor_sync(0xffffffffu, sum, 16)) * scale;
+                            if (part == 0) stg[bq * kMaxWinPerTile + h * wps + wi] = pw;
+                            ++wi;
+                        };
+                        auto add16 = [&](const float *v) {
+                            if (WIN >= 0) {
+                                ws += sumsq16(v);
+                                cnt += 16;
+                                if (cnt == a.t_int) {
+                                    emit(ws);
+                                    ws = 0.f;
+                                    cnt = 0;
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) {
+                                    ws = fmaf(v[i], v[i], ws);
+                                    if (++cnt == a.t_int) {
+                                        emit(ws);
+                                        ws = 0.f;
+                                        cnt = 0;
+                                    }
+                                }
+                            }
+                        };
+                        int col = 0;
+                        if (WIN > 0 && cols == 64) {
+                            uint32_t r[64];
+                            tmem_ld64r(taddr, r);
+                            release();
+#pragma unroll
+                            for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
+                                emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
+                            col = 64;
+                        } else if (WIN > 0 && cols % 128 == 0) {
+                            // 128 columns per load; the accumulator is released after the
+                            // last load, before the squares are summed
+                            for (; col < cols; col += 128) {
+                                uint32_t r[128];
+                                tmem_ld128(taddr + col, r);
+                                if (col + 128 == cols) release();
+#pragma unroll
+                                for (int k = 0; k < 128 / (WIN > 0 ? WIN : 128); ++k)
+                                    emit(sumsq_pk<(WIN > 0 ? WIN : 128)>(r + k * (WIN > 0 ? WIN : 128)));
+                            }
+                        }
+                        const int n64 = (cols - col) / 64, rem = (cols - col) % 64;   // rem is a multiple of 16
+                        for (int bt = 0; bt < n64; ++bt) {
+                            float v[64];
+                            tmem_ld64(taddr + col + bt * 64, v);
+                            if (bt == n64 - 1 && rem == 0) release();
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) add16(v + 16 * k);
+                        }
+                        for (col += n64 * 64; col < cols; col += 16) {
+                            float v[16];
+                            tmem_ld16(taddr + col, v);
+                            if (col + 16 == cols) release();
+                            add16(v);
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(b_sfull + 8 * sb);   // publishes the staged windows
                     }
                     if (++acc == a.nacc) acc = 0;
                 }
@@ -396,20 +553,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // writes each staged tile as one run of windows per beam
         uint32_t kt = 0;
         bool ok = true;
+        const bool vec = (a.T_o & 3) == 0 && (a.wpt & 3) == 0;
         for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
             int m0, gs;
             group_tiles(a, g, m0, gs);
             int c = c_first, tt = tt_first;
             for (long long ct = ct0; ct < ct1 && ok; ++ct) {
                 const int cg = a.c_base + c;
+                const int j0 = tt * a.wpt;
+                const int nj = min(a.wpt, a.T_o - j0);
                 for (int s = 0; s < gs; ++s, ++kt) {
                     const uint32_t sb = kt % kStageDepth;
                     if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
                     }
-                    store_tile(a, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), (m0 + s) * kBeamsPerMTile, cg, tt,
-                               lane);
+                    const float *stg = stage + sb * (kBeamsPerMTile * kMaxWinPerTile);
+                    const int b_tile0 = (m0 + s) * kBeamsPerMTile;
+                    if (vec && a.wpt == 4) {
+                        // one float4 per beam: lanes take beams lane and lane + 32
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int bl = lane + 32 * r;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && nj > 0) {
+                                const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile);
+                                *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o + j0) = v4;
+                            }
+                        }
+                    } else if (vec) {
+                        const int per = a.wpt >> 2;
+                        for (int i = lane; i < kBeamsPerMTile * per; i += 32) {
+                            const int bl = i / per, k = (i % per) * 4;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && k < nj) {
+                                const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile + k);
+                                *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o + j0 + k) = v4;
+                            }
+                        }
+                    } else {
+                        for (int i = lane; i < kBeamsPerMTile * a.wpt; i += 32) {
+                            const int bl = i / a.wpt, k = i % a.wpt;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && k < nj)
+                                a.out[((size_t)bb * a.c_total + cg) * a.T_o + j0 + k] = stg[bl * kMaxWinPerTile + k];
+                        }
+                    }
                     __syncwarp();
                     if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
                 }
@@ -430,46 +619,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ----------------------------------------------------------------- host side
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-static bool encode3(CUtensorMap *m, const void *ptr, cuuint64_t d0, cuuint64_t d1, cuuint64_t d2, int es, int box0,
-                    int box1)
-{
-    auto enc = tensor_map_encoder();
-    if (!enc) return false;
-    const CUtensorMapDataType dt = es == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    cuuint64_t dims[3] = {d0, d1, d2};
-    cuuint64_t strides[2] = {d0 * es, d0 * d1 * es};
-    cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, dt, 3, const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-bool encode_voltage_map(CUtensorMap *m, const void *x, int two_n, int T, int C, int es, int ke, int nt)
-{
-    return encode3(m, x, (cuuint64_t)two_n, (cuuint64_t)T, (cuuint64_t)C, es, ke, nt);
-}
-
-bool encode_weight_map(CUtensorMap *m, const void *w, int k_pad, int m_pad, int C, int es, int ke)
-{
-    return encode3(m, w, (cuuint64_t)k_pad, (cuuint64_t)m_pad, (cuuint64_t)C, es, ke, kRowsPerMTile);
-}
-
 static int gcd_i(int x, int y)
 {
     while (y) {
@@ -648,8 +797,6 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
-    ka.acc_in = nullptr;
-    ka.acc_out = nullptr;
     ka.err = p->d_err;
     if (ka.ct_total == 0) return cudaSuccess;
     if (!layout_ok(cfg, f.kb) || ka.gmax != (cfg.stream ? 0 : cfg.group)) {   // final guard before launch
