@@ -24,6 +24,7 @@ struct __align__(128) BatchJob {
     int C, t_tiles, mt, kb, ke;
     int T, T_o, B, b_pad;
     int t_shift;        // samples of window 0 that precede this chunk (0..T_int-1)
+    int ks_last;        // MMA k-steps (of 4) holding antennas in the last K block
     uint32_t idesc;
     const float *wscale;   // [C][b_pad] sigma^2, or NULL (unscaled formats)
     const float *wsig;

@@ -47,29 +47,43 @@ struct UnitPos {
     int j, c, tt, m;
 };
 
-// Walks this CTA's units (blockIdx.x, + gridDim.x, ...), tracking the job
-// and decoding positions.
+// Walks this CTA's units (blockIdx.x, + gridDim.x, ...), decoding positions.
+// The current job's scalars stay in registers; `fresh` tells the caller that
+// the job changed on the last step (so it reloads its own per-job fields).
 struct UnitWalk {
     const BatchArgs *a;
-    long long u;
-    int j;
+    long long u, unit0, end;
+    int j, mt, t_tiles;
+    bool fresh;
     __device__ void begin(const BatchArgs &args)
     {
         a = &args;
         u = blockIdx.x;
-        j = u < args.total_units ? job_of(args, u) : 0;
+        j = -1;
+        unit0 = end = 0;
+        mt = t_tiles = 1;
+        fresh = false;
     }
     __device__ bool next(UnitPos &p)
     {
         if (u >= a->total_units) return false;
-        while (u >= a->jobs[j].unit0 + a->jobs[j].units) ++j;
-        const BatchJob &J = a->jobs[j];
-        const int v = (int)(u - J.unit0);
+        fresh = false;
+        if (j < 0 || u >= end) {
+            j = j < 0 ? job_of(*a, u) : j + 1;
+            while (u >= a->jobs[j].unit0 + a->jobs[j].units) ++j;
+            const BatchJob &J = a->jobs[j];
+            unit0 = J.unit0;
+            end = J.unit0 + J.units;
+            mt = J.mt;
+            t_tiles = J.t_tiles;
+            fresh = true;
+        }
+        const int v = (int)(u - unit0);
         p.j = j;
-        p.m = v % J.mt;
-        const int r = v / J.mt;
-        p.tt = r % J.t_tiles;
-        p.c = r / J.t_tiles;
+        p.m = v % mt;
+        const int r = v / mt;
+        p.tt = r % t_tiles;
+        p.c = r / t_tiles;
         u += gridDim.x;
         return true;
     }
@@ -125,20 +139,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t cnt = 0, issued = 0;
-            int st = 0, pj = -1;
+            int st = 0;
             UnitWalk w;
             w.begin(a);
             UnitPos p;
             bool ok = true;
+            const CUtensorMap *xmap = nullptr, *wmap = nullptr;
+            int kbn = 0, ke = 0, t_shift = 0;
+            const uint32_t bytes = 16384 + a.nt * 128;
             while (ok && w.next(p)) {
-                const BatchJob &J = a.jobs[p.j];
-                if (p.j != pj) {
-                    prefetch_tensormap(&J.xmap);
-                    prefetch_tensormap(&J.wmap);
-                    pj = p.j;
+                if (w.fresh) {
+                    const BatchJob &J = a.jobs[p.j];
+                    xmap = &J.xmap;
+                    wmap = &J.wmap;
+                    prefetch_tensormap(xmap);
+                    prefetch_tensormap(wmap);
+                    kbn = J.kb;
+                    ke = J.ke;
+                    t_shift = J.t_shift;
                 }
-                const uint32_t bytes = 16384 + a.nt * 128;
-                for (int kb = 0; kb < J.kb; ++kb) {
+                for (int kb = 0; kb < kbn; ++kb) {
                     if (!mbar_wait(b_empty + 8 * st, ((cnt >> st) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
@@ -147,10 +167,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
                     issued |= 1u << st;
                     const uint32_t dst = sx + st * a.stage_bytes;
                     mbar_arrive_expect_tx(b_full + 8 * st, bytes);
-                    tma_load_3d(dst, &J.wmap, b_full + 8 * st, kb * J.ke, p.m * kRowsPerMTile, p.c);
+                    tma_load_3d(dst, wmap, b_full + 8 * st, kb * ke, p.m * kRowsPerMTile, p.c);
                     // window 0 starts t_shift samples before the chunk: those rows
                     // (negative time coordinates) read as zeros
-                    tma_load_3d(dst + 16384, &J.xmap, b_full + 8 * st, kb * J.ke, p.tt * a.nt - J.t_shift, p.c);
+                    tma_load_3d(dst + 16384, xmap, b_full + 8 * st, kb * ke, p.tt * a.nt - t_shift, p.c);
                     if (++st == a.xst) st = 0;
                 }
             }
@@ -168,8 +188,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
             w.begin(a);
             UnitPos p;
             bool ok = true;
+            int kbn = 0, ks_last = 4;
+            uint32_t idesc = 0;
             while (ok && w.next(p)) {
-                const BatchJob &J = a.jobs[p.j];
+                if (w.fresh) {
+                    const BatchJob &J = a.jobs[p.j];
+                    kbn = J.kb;
+                    ks_last = J.ks_last;
+                    idesc = J.idesc;
+                }
                 if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                     ok = false;
                     break;
@@ -177,7 +204,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
                 tpar ^= 1u << acc;
                 tc_fence_after();
                 const uint32_t d = tmem + acc * a.nt;
-                for (int kb = 0; kb < J.kb; ++kb) {
+                for (int kb = 0; kb < kbn; ++kb) {
                     if (!mbar_wait(b_full + 8 * st, (par >> st) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
@@ -185,12 +212,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
                     par ^= 1u << st;
                     tc_fence_after();
                     const uint32_t sw = sx + st * a.stage_bytes;
+                    // the last K block may hold fewer than 4 k-steps of antennas (the
+                    // rest is zero padding): those MMAs are skipped
+                    const int ksn = kb + 1 == kbn ? ks_last : 4;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
+                        if (ks >= ksn) break;
                         const uint64_t ad = sdesc_sw128(sw + ks * 32);
                         const uint64_t bd = sdesc_sw128(sw + 16384 + ks * 32);
-                        if (F8) mma_f8(d, ad, bd, J.idesc, (kb | ks) != 0);
-                        else mma_f16(d, ad, bd, J.idesc, (kb | ks) != 0);
+                        if (F8) mma_f8(d, ad, bd, idesc, (kb | ks) != 0);
+                        else mma_f16(d, ad, bd, idesc, (kb | ks) != 0);
                     }
                     mma_commit(b_empty + 8 * st);
                     if (++st == a.xst) st = 0;
@@ -217,8 +248,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         UnitWalk w;
         w.begin(a);
         UnitPos p;
+        TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, 0, 0, 0, 0, 0, nullptr, nullptr, nullptr};
         while (w.next(p)) {
-            const BatchJob &J = a.jobs[p.j];
+            if (w.fresh) {
+                const BatchJob &J = a.jobs[p.j];
+                o.T = J.T;
+                o.T_o = J.T_o;
+                o.B = J.B;
+                o.b_pad = J.b_pad;
+                o.c_total = J.C;
+                o.wscale = J.wscale;
+                o.wsig = J.wsig;
+                o.out = J.out;
+            }
             if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
             tpar ^= 1u << acc;
             const uint32_t sb = kt % kStageDepth;
@@ -232,8 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
             if (!active) {
                 tile_release(tempty, lane);
             } else {
-                const TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, J.T, J.T_o, J.B, J.b_pad, J.C, J.wscale, J.wsig, J.out};
-                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < J.B, p.c,
+                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < o.B, p.c,
                                     stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
             }
             ++kt;
@@ -245,12 +286,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         UnitWalk w;
         w.begin(a);
         UnitPos p;
+        TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, 0, 0, 0, 0, 0, nullptr, nullptr, nullptr};
         while (w.next(p)) {
-            const BatchJob &J = a.jobs[p.j];
+            if (w.fresh) {
+                const BatchJob &J = a.jobs[p.j];
+                o.T = J.T;
+                o.T_o = J.T_o;
+                o.B = J.B;
+                o.b_pad = J.b_pad;
+                o.c_total = J.C;
+                o.out = J.out;
+                o.acc_in = J.acc_in;
+                o.acc_out = J.acc_out;
+            }
             const uint32_t sb = kt % kStageDepth;
             if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
-            const TileOut o{a.nt,  a.nsplit, a.wpt, a.t_int,  J.T,      J.T_o,   J.B,
-                            J.b_pad, J.C,      J.wscale, J.wsig, J.out, J.acc_in, J.acc_out};
             store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), p.m * kBeamsPerMTile, p.c, p.tt, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
@@ -394,6 +444,9 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
     J->B = p->B;
     J->b_pad = f.b_pad;
     J->t_shift = t_shift;
+    const int rem = (2 * p->N) % f.ke;   // operand elements in a partly padded last K block
+    const int per_step = f.ke / 4;       // elements per MMA k-step (16 x 16-bit or 32 x 8-bit = 32 bytes)
+    J->ks_last = rem ? (rem + per_step - 1) / per_step : 4;
     const uint32_t fmt = (f.op == kOpBF16) ? 1u : 0u;
     J->idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(core.nt >> 3) << 17) |
                ((uint32_t)(kRowsPerMTile >> 4) << 24);
