@@ -417,6 +417,34 @@ bf_status bf_server_destroy(bf_server *server);
 double bf_server_now(void);
 
 /*
+ * bf_detect — a consumer of the integrated powers that keeps them on the
+ * device (the transient-detection stages after the beamformer, Section 3,
+ * Table 3: detrending and thresholding; the paper gives no formulas, so this
+ * is the library's reading): for every beam b and channel c over the n_win
+ * windows of d_power [B][C][n_win] (device, float),
+ *   mu = mean_j P,  sigma = sqrt(mean_j (P - mu)^2)   (FP64),
+ *   z[b][c][j] = (P - mu) / sigma   (0 where sigma = 0),
+ * written to d_z (device, float [B][C][n_win], or NULL), and every (b, c, j)
+ * with z > k_sigma appended to d_hits (device, int [max_hits][3], in no
+ * particular order); *d_n_hits (device int) receives the number of hits,
+ * which may exceed max_hits (only the first max_hits are stored).
+ * Asynchronous on `stream`.  Errors: BF_ERR_ARG.
+ */
+bf_status bf_detect(const float *d_power, int n_beam, int n_chan, int n_win, float k_sigma,
+                    float *d_z, int *d_hits, int max_hits, int *d_n_hits, void *stream);
+
+/*
+ * bf_selftest_timeout — diagnostic of the failure path: launches a one-warp
+ * kernel that waits, with the bounded wait every pipelined kernel of the
+ * library uses, on an mbarrier that nothing arrives at.  After limit_ms
+ * (0 < limit_ms <= 10000) the wait gives up, records the timeout in a status
+ * word and the kernel returns; the context stays usable.  Synchronous on
+ * `stream`.  Returns BF_ERR_TIMEOUT when the path works as designed,
+ * BF_ERR_CUDA if the wait did not report, BF_ERR_ARG for a bad limit.
+ */
+bf_status bf_selftest_timeout(double limit_ms, void *stream);
+
+/*
  * bf_execute_nct_static — bf_execute for an antenna-major (BF_LAYOUT_NCT)
  * tensor-core plan that allocates nothing.  The paper has no counterpart: it
  * exists for callers that cannot allocate device memory when they execute

@@ -241,3 +241,20 @@ def corner_turn(x_nct, perm=None):
     if perm is not None:
         x = x[np.asarray(perm)]
     return np.ascontiguousarray(np.moveaxis(x, 0, 2))
+
+
+def detect(P, k_sigma: float):
+    """Detrend-and-threshold consumer of the integrated powers, the reading of
+    the 'detrending' and 'RFI thresholding' stages that follow the beamformer
+    in the transient pipeline of Section 3 (Table 3; the paper gives no
+    formula for them).  For every beam b and channel c, over the chunk's
+    windows j:  mu = mean_j P[b][c][j],  sigma = sqrt(mean_j (P - mu)^2)
+    (population), z[b][c][j] = (P - mu) / sigma (0 where sigma = 0), and the
+    hits are the (b, c, j) with z > k_sigma.  Returns (z as float64 [B][C][T_o],
+    hits as a sorted int array [n][3])."""
+    P = np.asarray(P, dtype=np.float64)
+    mu = P.mean(axis=2, keepdims=True)
+    sd = np.sqrt(((P - mu) ** 2).mean(axis=2, keepdims=True))
+    z = np.where(sd > 0, (P - mu) / np.where(sd > 0, sd, 1.0), 0.0)
+    hits = np.argwhere(z > k_sigma)
+    return z, hits

@@ -78,6 +78,8 @@ SIGNATURES = {
     "bf_server_stats": [_P, ctypes.POINTER(bf_server_counters)],
     "bf_server_destroy": [_P],
     "bf_server_now": [],
+    "bf_detect": [_P, _I, _I, _I, ctypes.c_float, _P, _P, _I, _P, _P],
+    "bf_selftest_timeout": [ctypes.c_double, _P],
     "bf_execute_nct_static": [_P, _P, _I, _P, _P],
 }
 
@@ -281,6 +283,31 @@ def bf_server_destroy(server: int):
 
 def bf_server_now() -> float:
     return _lib.bf_server_now()
+
+
+def bf_detect(d_power: int, n_beam: int, n_chan: int, n_win: int, k_sigma: float, d_z: int, d_hits: int,
+              max_hits: int, d_n_hits: int, stream: int = 0):
+    _check(_lib.bf_detect(d_power or None, n_beam, n_chan, n_win, float(k_sigma), d_z or None, d_hits or None,
+                          max_hits, d_n_hits or None, stream or None))
+
+
+def detect(power, k_sigma: float, max_hits: int = 1 << 16, want_z: bool = True, stream=None):
+    """Torch helper around bf_detect: power is a device float32 tensor
+    [B][C][T_o]; returns (z or None, hits [n][3] int32 tensor, total hit count)."""
+    import torch
+    B, C, W = power.shape
+    s = stream if stream is not None else torch.cuda.current_stream()
+    z = torch.empty_like(power) if want_z else None
+    hits = torch.empty((max_hits, 3), dtype=torch.int32, device=power.device)
+    n = torch.zeros(1, dtype=torch.int32, device=power.device)
+    bf_detect(power.data_ptr(), B, C, W, k_sigma, z.data_ptr() if want_z else 0, hits.data_ptr(), max_hits,
+              n.data_ptr(), s.cuda_stream)
+    total = int(n.item())
+    return z, hits[:min(total, max_hits)], total
+
+
+def bf_selftest_timeout(limit_ms: float = 50.0, stream: int = 0):
+    _check(_lib.bf_selftest_timeout(float(limit_ms), stream or None))
 
 
 # ------------------------------------------------------------ torch helper

@@ -98,6 +98,8 @@ def test_null_and_bad_handles(bf):
     assert lib.bf_server_stats(None, None) == bf.BF_ERR_ARG
     assert lib.bf_server_destroy(None) == bf.BF_OK
     assert lib.bf_server_now() > 0.0
+    assert lib.bf_selftest_timeout(0.0, None) == bf.BF_ERR_ARG
+    assert lib.bf_selftest_timeout(1e9, None) == bf.BF_ERR_ARG
     out = ctypes.c_void_p(123)
     assert lib.bf_plan_create(ctypes.byref(out), 0, None, None, 0, None, 0, None, 0, 0, 0, None) == bf.BF_ERR_ARG
     assert out.value is None

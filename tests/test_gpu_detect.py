@@ -1,0 +1,76 @@
+"""GPU parity of the on-device detrend-and-threshold consumer (bf_detect)
+against the FP64 oracle, and an end-to-end case: a burst from one direction
+in a few windows is found at that beam and those windows, with the powers
+never leaving the device."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import small_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1412_4907_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("B,C,W", [(37, 5, 300), (1, 1, 1), (64, 3, 33), (5, 2, 1000)])
+def test_detect_matches_oracle(bf, B, C, W):
+    g = np.random.default_rng(B * 1000 + W)
+    P = g.exponential(100.0, size=(B, C, W)).astype(np.float32)   # |B|^2 of noise is exponential
+    P[B // 2, C - 1, W // 3] *= 40.0
+    k = 4.0
+    z, hits, total = bf.detect(torch.from_numpy(P).cuda(), k)
+    torch.cuda.synchronize()
+    z_ref, hits_ref = oracle.detect(P, k)
+    assert np.max(np.abs(z.cpu().numpy() - z_ref)) <= 1e-5 * max(1.0, np.max(np.abs(z_ref)))
+    # decisions within 1e-6 of the threshold could go either way in FP64 order; none here
+    assert np.min(np.abs(z_ref - k)) > 1e-6
+    got = sorted(map(tuple, hits.cpu().numpy().tolist()))
+    assert total == len(hits_ref) and got == sorted(map(tuple, hits_ref.tolist()))
+
+
+def test_detect_overflow_and_empty(bf):
+    P = np.zeros((3, 2, 10), dtype=np.float32)
+    P[:, :, 5] = 1.0   # every row has a spike: 6 hits
+    z, hits, total = bf.detect(torch.from_numpy(P).cuda(), 2.0, max_hits=4)
+    assert total == 6 and hits.shape[0] == 4
+    assert all(int(j) == 5 for _, _, j in hits.cpu().numpy())
+    z, hits, total = bf.detect(torch.zeros((2, 2, 0), device="cuda"), 1.0)
+    assert total == 0
+
+
+def test_beamform_then_detect_on_device(bf):
+    """A 20 dB burst from beam 37's direction in window 5 of 16: after
+    beamforming and detection on the device, beam 37's hits are exactly that
+    window in every channel (one spike in 16 windows has z = sqrt(15) = 3.87),
+    and hits elsewhere are mostly the same window seen by other beams."""
+    scene, dirs, t_int = synth.config1()
+    scene = synth.Scene(pos=scene.pos, freqs=scene.freqs[:4], n_samp=1024, seed=9, noise_sigma=scene.noise_sigma,
+                        sources=[])
+    x = synth.voltages(scene, synth.C32).view(np.complex64).copy()          # [C][T][N] noise
+    tau = scene.pos @ dirs[37] / 299792458.0
+    g = np.random.default_rng(2)
+    for w in (5,):
+        t0, t1 = w * 64, (w + 1) * 64
+        s = (g.standard_normal((4, 64)) + 1j * g.standard_normal((4, 64))) * np.sqrt(100.0 / 2)
+        ph = np.exp(2j * np.pi * np.outer(scene.freqs, tau))                  # [C][N]
+        x[:, t0:t1, :] += (s[:, :, None] * ph[:, None, :]).astype(np.complex64)
+    xh = x.astype(np.complex64).view(np.float32).astype(np.float16)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C16F, 64)
+    P = plan.execute(torch.from_numpy(np.ascontiguousarray(xh)).cuda())
+    z, hits, total = bf.detect(P, 3.0)
+    torch.cuda.synchronize()
+    h = hits.cpu().numpy()
+    at37 = {(int(c), int(j)) for b, c, j in h if b == 37}
+    assert at37 == {(c, 5) for c in range(4)}
+    stray = sum(1 for _, _, j in h if j != 5)   # noise windows of rows the burst does not dominate
+    assert stray <= 0.02 * P.numel()
+    plan.close()

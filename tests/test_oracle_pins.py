@@ -323,3 +323,31 @@ def test_planted_mistakes_are_caught(tmp_path):
             assert caught >= 1, f"planted mistake not caught: {name}"
     finally:
         oracle._lib = saved
+
+
+# ------------------------------------------------ downstream detect-and-threshold
+def test_detect_single_spike_closed_form():
+    """A flat series of n windows with one spike: whatever the level a and the
+    spike height d, z(spike) = sqrt(n - 1) and every other z = -1/sqrt(n - 1)
+    (mean a + d/n, population deviation d sqrt(n - 1)/n)."""
+    for n, a, d, j0 in ((16, 3.0, 5.0, 4), (244, 1e4, 0.5, 200), (2, 7.0, 1.0, 0)):
+        P = np.full((2, 3, n), a)
+        P[1, 2, j0] += d
+        z, hits = oracle.detect(P, 0.9 * np.sqrt(n - 1))
+        assert abs(z[1, 2, j0] - np.sqrt(n - 1)) < 1e-9 * np.sqrt(n)
+        others = np.delete(z[1, 2], j0)
+        assert np.allclose(others, -1.0 / np.sqrt(n - 1), rtol=0, atol=1e-9)
+        assert np.all(z[0] == 0.0) and np.all(z[1, :2] == 0.0)   # flat rows: sigma = 0 -> z = 0
+        assert hits.tolist() == [[1, 2, j0]]
+
+
+def test_detect_gaussian_tail_rate():
+    """Standard normal windows: the fraction above 3 sigma is the normal tail
+    probability 1.35e-3 (binomial 5-sigma bounds)."""
+    g = np.random.default_rng(3)
+    P = g.standard_normal((20, 50, 1000))
+    z, hits = oracle.detect(P, 3.0)
+    n = P.size
+    p = 0.5 * math.erfc(3.0 / math.sqrt(2.0))
+    assert abs(len(hits) - n * p) < 5 * math.sqrt(n * p * (1 - p))
+    assert abs(z.mean()) < 1e-12 and abs((z ** 2).mean() - 1.0) < 1e-12
