@@ -144,6 +144,24 @@ def dist_env():
     return world, rank, local
 
 
+def shard_range(n: int, world: int, rank: int):
+    """Contiguous share [lo, hi) of n independent units (channels) for one rank:
+    the first n % world ranks take one extra."""
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (every rank gets it); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_rate(scene, dirs, t_int, n_chan, threads=0, x_cache=None):
     """FP64 oracle (plain C, one thread per channel range) on the first
     ``n_chan`` channels and the given beams: returns (TFLOP/s, seconds)."""
@@ -191,19 +209,20 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(scene, dirs, t_int),
+            "config": config_dict(scene, dirs, t_int, args.scaling),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def config_dict(scene, dirs, t_int):
+def config_dict(scene, dirs, t_int, scaling="weak"):
     return {"workload": f"real-time FP16 chunk: 32-antenna BEST-2 grid, {scene.n_chan} channels x 15625 "
                         "samples, 1024 beams, T_int 64",
             "n_ant": scene.n_ant, "n_chan": scene.n_chan, "n_beam": int(dirs.shape[0]),
             "n_samp": scene.n_samp, "t_int": t_int, "input": "c16f, [c][t][n] (no corner turn)",
             "l2": "no flush: voltages (2.05 GB) and weights (0.27 GB) exceed the 129 MB L2",
-            "parallelism": "channels: one independent chunk per GPU, no collective"}
+            "parallelism": ("channels: one independent chunk per GPU, no collective" if scaling == "weak" else
+                            "channels: contiguous channel ranges of one chunk per GPU, no collective")}
 
 
 def run_ours(args):
@@ -221,6 +240,10 @@ def run_ours(args):
     scene, dirs, t_int = synth.config2()
     if args.channels:   # a band subset with the same per-channel shape (profiling captures)
         scene.freqs = scene.freqs[:args.channels]
+    C_job = scene.n_chan
+    if args.scaling == "strong" and world > 1:   # one band split into contiguous channel ranges
+        lo, hi = shard_range(C_job, world, rank)
+        scene.freqs = scene.freqs[lo:hi]
     N, C, B, T = scene.n_ant, scene.n_chan, dirs.shape[0], scene.n_samp
     T_o = T // t_int
     F = flops(N, B, C, T)
@@ -266,12 +289,11 @@ def run_ours(args):
     total_ms = t_start.elapsed_time(t_end)
     w_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     k_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     ms_step = total_ms / args.steps
-    value = world * F / (ms_step * 1e-3) / 1e12
+    # units all ranks processed / slowest rank's time
+    F_job = flops(N, B, C_job, T) if args.scaling == "strong" else world * F
+    value = F_job / (ms_step * 1e-3) / 1e12
 
     # end to end through the public host-memory call (copies inside the timed region)
     e2e = None
@@ -288,12 +310,8 @@ def run_ours(args):
         for i in range(n_e2e):
             bf.bf_weights(plan.handle, dirs_alt[i % 2])
             bf.bf_execute_host(plan.handle, xh.data_ptr(), T, ph.data_ptr())
-        e2e_s = (time.perf_counter() - t0) / n_e2e
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * F / e2e_s / 1e12, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, dist, "cuda")
+        e2e = {"value": F_job / e2e_s / 1e12, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": int(x_host.nbytes), "d2h_bytes_per_step": int(B * C * T_o * 4)}
         del xh, ph
 
@@ -345,9 +363,9 @@ def run_ours(args):
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n_chan} of 1024 channels (all beams, all samples), {dt:.1f} s"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": args.scaling,
             "vs_baseline": None, "dtype": "f16", "data": "synthetic: seeded complex Gaussian noise + 3 plane waves",
-            "config": config_dict(scene, dirs, t_int), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "config": config_dict(scene, dirs, t_int, args.scaling), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps * 1,
             "breakdown_ms": {"weights": w_ms, "beamform": k_ms},
             "fp32_form": fp32, "clocks": clk}
@@ -744,6 +762,8 @@ def main():
                     help="precision sweep on the config-3 shape (one JSON line per mode) instead of the benchmark")
     ap.add_argument("--batched", action="store_true",
                     help="batched uneven launch of 48 sub-array jobs (one JSON line per variant)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank beamforms its own chunk; strong: the chunk's channels are split over ranks")
     ap.add_argument("--batched-chan-div", type=int, default=1,
                     help="divide every job's channel count (smaller case of the same jobs, for profiling)")
     ap.add_argument("--serve", action="store_true",
