@@ -643,14 +643,32 @@ def run_serve(args):
         rings.append([torch.empty(B * C * (SERVE_RATE_HZ // 64 + 1), dtype=torch.float32).pin_memory()
                       for _ in range(4)])
     torch.cuda.synchronize()
-    server = bf.Server(plans, mem_bytes=int(args.serve_mem * 2**30), max_steps=3)
+    server = bf.Server(plans, mem_bytes=int(args.serve_mem * 2**30), max_steps=args.serve_steps)
     for i in range(len(SERVE_CONFIGS)):   # warm-up: one chunk per stream
         server.submit(i, pools[i], rings[i][0], n_samp=256)
     server.drain(120000)
     server.poll(64)
     base = server.stats()
     arrivals = serve_arrivals(args.serve_rate, args.serve_seconds)
+    series, stop = [], [False]
+
+    def sample():   # link and device counters every 0.5 s, to see the rates over the run
+        last = server.stats()
+        while not stop[0]:
+            time.sleep(0.5)
+            st_ = server.stats()
+            db = st_["copy_in_bytes"] - last["copy_in_bytes"]
+            dm = st_["copy_in_ms"] - last["copy_in_ms"]
+            series.append({"t": round(bf.bf_server_now() - t0, 2), "copy_gbps": round(db / (dm * 1e-3) / 1e9, 1)
+                           if dm else None, "copy_busy": round(dm * 1e-3 / 0.5, 2),
+                           "kernel_busy": round((st_["kernel_ms"] - last["kernel_ms"]) * 1e-3 / 0.5, 2),
+                           "done": st_["completed"] - base["completed"]})
+            last = st_
+
+    import threading
     t0 = bf.bf_server_now() + 0.05
+    sampler = threading.Thread(target=sample, daemon=True)
+    sampler.start()
     ids = {}
     for k, (ta, cfg, T) in enumerate(arrivals):
         due = t0 + ta
@@ -664,6 +682,8 @@ def run_serve(args):
         ids[i] = (due, cfg, T)
     t_sub_end = bf.bf_server_now()
     server.drain(600000)
+    stop[0] = True
+    sampler.join()
     done = {}
     while len(done) < len(ids):
         for c in server.poll(1024, 1000):
@@ -708,10 +728,11 @@ def run_serve(args):
            "steps": steps, "mean_chunks_per_step": len(ids) / max(1, steps), "max_chunks_per_step": st["max_jobs_per_step"],
            "arena_gb": st["arena_bytes"] / 2**30, "arena_peak_gb": st["arena_peak"] / 2**30,
            "submit_lag_s": t_sub_end - (t0 + arrivals[-1][0]) if arrivals else 0.0,
+           "series_0p5s": series,
            "config": {"workload": "6 streams (32,1024,1024,f16) (64,64,4096,i8) (128,512,2048,f16) (256,2048,512,i8) "
                                   "(512,8192,256,f16) (512,256,4096,i8) as (N,B,C,dtype); Poisson arrivals, chunk "
                                   "0.25-1 s at 1024 samples/s per channel, T_int 64 with the open window carried",
-                      "tile_t": st["tile_t"]}}
+                      "tile_t": st["tile_t"], "max_steps": args.serve_steps, "arena_gib": args.serve_mem}}
     print(json.dumps(res), flush=True)
     for p in plans:
         p.close()
@@ -771,6 +792,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=400.0, help="chunk arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="seconds of arrivals")
     ap.add_argument("--serve-mem", type=float, default=48.0, help="server arena in GiB")
+    ap.add_argument("--serve-steps", type=int, default=3, help="server steps in flight (1..8)")
     ap.add_argument("--serve-fp32-chunks", type=int, default=40, help="chunks for the FP32 single-job comparison")
     ap.add_argument("--channels", type=int, default=0,
                     help="run only the first C channels (same per-channel shape; for profiling)")
