@@ -770,6 +770,64 @@ def run_serve(args):
         p.close()
 
 
+def run_aux(args):
+    """The HBM-bound kernels on the real-time chunk's sizes (32 antennas, 1024
+    channels, 15625 samples, 1024 beams, T_int 64): corner turn, incoherent
+    beam, detrend-and-threshold of the powers.  One JSON line per kernel:
+    algorithmic bytes / CUDA-event time against the measured copy bandwidth."""
+    import torch
+
+    import paper_1412_4907_gb300 as bf
+    torch.cuda.set_device(0)
+    scene, dirs, t_int = synth.config2()
+    N, C, B, T = scene.n_ant, scene.n_chan, dirs.shape[0], scene.n_samp
+    T_o = T // t_int
+    pk, pk_kind = peaks()
+    hbm = pk["hbm_gbs"]
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    x_nct = (torch.randn((N, C, T, 2), generator=g, device="cuda") * 0.7071).half()
+    x_ctn = torch.empty((C, T, N, 2), dtype=torch.float16, device="cuda")
+    P = torch.rand((B, C, T_o), generator=g, device="cuda")
+    z = torch.empty_like(P)
+    hits = torch.empty((1 << 16, 3), dtype=torch.int32, device="cuda")
+    nh = torch.zeros(1, dtype=torch.int32, device="cuda")
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C16F, t_int, stream=stream)
+    inc = torch.empty((C, T_o), dtype=torch.float32, device="cuda")
+    x_ctn_in = torch.from_numpy(synth.voltages(scene, synth.C16F)).cuda()
+    cases = [
+        ("corner turn [N][C][T] -> [C][T][N], FP16", 2 * x_nct.numel() * 2,
+         lambda: bf.bf_corner_turn(x_nct.data_ptr(), bf.BF_C16F, x_ctn.data_ptr(), bf.BF_C16F, N, C, T, None,
+                                   stream.cuda_stream)),
+        ("incoherent beam (sum of |X|^2 over antennas), FP16 in", x_ctn_in.numel() * 2 + inc.numel() * 4,
+         lambda: bf.bf_execute_incoherent(plan.handle, x_ctn_in.data_ptr(), T, inc.data_ptr(), stream.cuda_stream)),
+        ("detrend + threshold of the powers (bf_detect, z written)", P.numel() * 8,
+         lambda: bf.bf_detect(P.data_ptr(), B, C, T_o, 6.0, z.data_ptr(), hits.data_ptr(), 1 << 16, nh.data_ptr(),
+                              stream.cuda_stream)),
+    ]
+    for name, nbytes, fn in cases:
+        for _ in range(3):
+            fn()
+        n = 10
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b_.record(stream)
+        b_.synchronize()
+        ms = a.elapsed_time(b_) / n
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        print(json.dumps({"metric": "HBM-bound kernel: algorithmic GB/s", "kernel": name, "value": gbs,
+                          "unit": "GB/s", "ms": ms, "bytes": nbytes,
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                       "frac": gbs / hbm, "peak_source": f"hbm_gbs {pk_kind}"},
+                          "config": {"workload": "real-time chunk sizes: 32 antennas, 1024 channels, 15625 samples, "
+                                                 "1024 beams, T_int 64",
+                                     "l2": "no flush: every buffer exceeds the 129 MB L2"}}), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -787,6 +845,8 @@ def main():
                     help="weak: every rank beamforms its own chunk; strong: the chunk's channels are split over ranks")
     ap.add_argument("--batched-chan-div", type=int, default=1,
                     help="divide every job's channel count (smaller case of the same jobs, for profiling)")
+    ap.add_argument("--aux", action="store_true",
+                    help="HBM-bound kernels (corner turn, incoherent beam, detection) on the chunk's sizes")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream of 6 configurations with Poisson arrivals (p50/p99 latency)")
     ap.add_argument("--serve-rate", type=float, default=400.0, help="chunk arrivals per second")
@@ -806,6 +866,8 @@ def main():
         run_batched(args)
     elif args.serve:
         run_serve(args)
+    elif args.aux:
+        run_aux(args)
     else:
         run_ours(args)
 

@@ -326,9 +326,9 @@ bf_status bf_batch_destroy(bf_batch *batch);
  * (CTN, the plan's dtype) of any length.  Chunks are submitted from host
  * memory as they arrive; a scheduler thread admits them into a device arena
  * of fixed size as memory frees up, runs each step (at most one chunk per
- * stream, any mix of streams) as one batched tensor-core launch, overlaps the
- * copies of the next step with the current launch, and copies the powers back
- * into host memory.  The weights (in the plans) and the open integration
+ * stream, any mix of streams) as one batched tensor-core launch, and copies
+ * the powers back into host memory.  A chunk's copy to the device starts as
+ * soon as it is admitted, so copies overlap the launches of earlier chunks.  The weights (in the plans) and the open integration
  * window of every stream stay on the device: a chunk completes the window the
  * previous chunk of its stream left open (Section 2.1 integration across
  * buffer boundaries, Section 3 real-time operation), so a stream integrates
@@ -351,7 +351,7 @@ typedef struct bf_completion {
     int step;            /* scheduler step that computed it */
     int n_samp;          /* samples per channel in the chunk */
     double t_submit;     /* bf_server_submit returned */
-    double t_start;      /* its step's copies were enqueued */
+    double t_start;      /* admitted: its copy to the device was enqueued */
     double t_done;       /* its powers were in host memory */
 } bf_completion;
 
@@ -391,9 +391,10 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
 bf_status bf_server_submit(bf_server *server, int config, const void *h_voltages, int n_samp,
                            float *h_power, long long *id);
 
-/* bf_server_pause — paused != 0: admit nothing until resumed (submitted
- * chunks queue; steps already enqueued finish), for instance to hold
- * dispatch while the caller prepares a burst.  bf_server_destroy resumes. */
+/* bf_server_pause — paused != 0: admit and dispatch nothing until resumed
+ * (submitted chunks queue; steps already enqueued finish), for instance to
+ * hold dispatch while the caller prepares a burst.  bf_server_destroy
+ * resumes. */
 bf_status bf_server_pause(bf_server *server, int paused);
 
 /* bf_server_poll — move up to `max` completions (oldest first) into out[],
@@ -422,8 +423,8 @@ double bf_server_now(void);
  * Table 3: detrending and thresholding; the paper gives no formulas, so this
  * is the library's reading): for every beam b and channel c over the n_win
  * windows of d_power [B][C][n_win] (device, float),
- *   mu = mean_j P,  sigma = sqrt(mean_j (P - mu)^2)   (FP64),
- *   z[b][c][j] = (P - mu) / sigma   (0 where sigma = 0),
+ *   mu = mean_j P,  sigma = sqrt(mean_j (P - mu)^2)   (per-row sums in FP64),
+ *   z[b][c][j] = (P - mu) / sigma   (FP32; 0 where sigma = 0),
  * written to d_z (device, float [B][C][n_win], or NULL), and every (b, c, j)
  * with z > k_sigma appended to d_hits (device, int [max_hits][3], in no
  * particular order); *d_n_hits (device int) receives the number of hits,

@@ -22,6 +22,7 @@ struct __align__(128) BatchJob {
     long long unit0;    // first global unit of the job
     long long units;    // C x t_tiles x mt
     int C, t_tiles, mt, kb, ke;
+    int c_base, c_total;   // weight / output channel of the job's channel 0; output channel count
     int T, T_o, B, b_pad;
     int t_shift;        // samples of window 0 that precede this chunk (0..T_int-1)
     int ks_last;        // MMA k-steps (of 4) holding antennas in the last K block
@@ -46,10 +47,12 @@ struct BatchCore {
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t);
 
 // Fills one job.  x_mma: the voltages as the MMA reads them (the FP16
-// expansion for 8/4-bit integer inputs).  T_o, t_tiles and units follow from
-// T, t_shift and whether acc_out is given.
+// expansion for 8/4-bit integer inputs), [c_count][T][2N] for the plan's
+// channels c_base .. c_base + c_count - 1 (c_count < 0: all channels).  T_o,
+// t_tiles and units follow from T, t_shift and whether acc_out is given.
 bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, const void *x_mma, int T,
-                         float *out, int t_shift, const float *acc_in, float *acc_out);
+                         float *out, int t_shift, const float *acc_in, float *acc_out, int c_base = 0,
+                         int c_count = -1);
 
 // Numbers the units of jobs[0..n) in order; returns the total.
 long long batch_index(BatchJob *jobs, int n);
@@ -57,5 +60,10 @@ long long batch_index(BatchJob *jobs, int n);
 // One persistent launch over the table (already in device memory).
 cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
                               unsigned *d_err, cudaStream_t s);
+
+// One persistent launch of a single job passed by value (kernel parameter
+// space): no table copy, so it is stream-ordered and capturable like any
+// launch.  Used by the single-plan path for large antenna counts.
+cudaError_t batch_core_launch_one(const BatchCore &core, const BatchJob &job, unsigned *d_err, cudaStream_t s);
 
 }  // namespace bfi

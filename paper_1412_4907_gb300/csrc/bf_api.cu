@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 
+#include "batch.h"
 #include "bf_internal.h"
 
 namespace bfi {
@@ -64,6 +65,7 @@ static void plan_free(bf_plan *p)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     if (p->stream2) cudaStreamDestroy(p->stream2);
     if (p->stream3) cudaStreamDestroy(p->stream3);
+    delete p->bcore;
     delete p;
 }
 
@@ -318,6 +320,23 @@ static bf_status run_range(bf_plan *p, const void *x, int c_base, int c_launch, 
         BF_CUDA(launch_expand_to_f16(xin, p->dtype, scr, (long long)n_samp, p->N, s), "integer expansion");
         xin = scr;
     }
+    if (mode == 0 && p->tc.stream) {
+        // large antenna counts: the batched kernel's streamed pipeline with one
+        // job (its CTAs walk neighbouring tiles of one channel together, so the
+        // weight and voltage tiles are shared in L2)
+        if (!p->bcore) {
+            BatchCore core;
+            bf_plan *const one[1] = {p};
+            bf_status st = batch_core_init(&core, one, 1, p->tc.nt);
+            if (st != BF_OK) return st;
+            p->bcore = new BatchCore(core);
+        }
+        BatchJob J;
+        bf_status st = batch_fill_job(*p->bcore, &J, p, xin, T, out, 0, nullptr, nullptr, c_base, c_launch);
+        if (st != BF_OK) return st;
+        BF_CUDA(batch_core_launch_one(*p->bcore, J, p->d_err, s), "tensor-core kernel (streamed)");
+        return BF_OK;
+    }
     TcArgs ta;
     ta.x = xin;
     ta.c_base = c_base;
@@ -475,6 +494,8 @@ bf_status bf_plan_set_tiles(bf_plan *p, int tile_t, int group_tiles, int x_stage
     if (!tc_choose(p, req, &cfg, &why)) return set_error(BF_ERR_UNSUPPORTED, why);
     p->tc = cfg;
     p->tc_req = req;
+    delete p->bcore;   // re-derived from the new tiling on the next streamed launch
+    p->bcore = nullptr;
     return BF_OK;
 }
 

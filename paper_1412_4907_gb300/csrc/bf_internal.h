@@ -12,6 +12,7 @@
 #include "bf.h"
 
 namespace bfi {
+struct BatchCore;
 
 constexpr double kC0 = 299792458.0;      // m/s
 constexpr int kRowsPerMTile = 128;       // tensor-core tile rows (MMA M)
@@ -97,6 +98,7 @@ struct bf_plan {
     float *d_wsig = nullptr;          // [C][b_pad] sigma_b
 
     bfi::TcConfig tc;
+    bfi::BatchCore *bcore = nullptr;  // streamed power path (large K): the batched kernel, one job
 
     void *d_scratch = nullptr;        // corner-turn / expansion output
     size_t scratch_bytes = 0;

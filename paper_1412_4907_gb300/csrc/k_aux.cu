@@ -88,11 +88,52 @@ __global__ void k_corner(const Tin *__restrict__ in, Tout *__restrict__ out, int
     }
 }
 
+// 4-byte samples (FP16 / BF16 complex), 16-byte accesses on both sides: a
+// block turns 32 antennas x 64 samples of one channel.  Needs T % 4 == 0,
+// N % 4 == 0 and 16-byte aligned buffers (every row then starts aligned).
+__global__ void k_corner4v(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int N, int C, int T,
+                           const int *__restrict__ perm)
+{
+    __shared__ uint32_t tile[32][65];   // [antenna][sample], padded
+    const int t0 = blockIdx.x * 64, n0 = blockIdx.y * 32, c = blockIdx.z;
+    for (int v = threadIdx.x; v < 512; v += blockDim.x) {
+        const int j = v >> 4, q = v & 15;   // antenna row j, samples 4q .. 4q+3
+        const int n = n0 + j, t = t0 + 4 * q;
+        if (n < N && t < T) {   // T % 4 == 0: the whole vector is in range
+            const int src = perm ? perm[n] : n;
+            const uint4 x = *reinterpret_cast<const uint4 *>(in + ((size_t)src * C + c) * T + t);
+            tile[j][4 * q] = x.x;
+            tile[j][4 * q + 1] = x.y;
+            tile[j][4 * q + 2] = x.z;
+            tile[j][4 * q + 3] = x.w;
+        }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < 512; v += blockDim.x) {
+        const int i = v >> 3, q = v & 7;    // sample t0 + i, antennas 4q .. 4q+3
+        const int t = t0 + i, n = n0 + 4 * q;
+        if (t < T && n < N) {   // N % 4 == 0
+            uint4 y;
+            y.x = tile[4 * q][i];
+            y.y = tile[4 * q + 1][i];
+            y.z = tile[4 * q + 2][i];
+            y.w = tile[4 * q + 3][i];
+            *reinterpret_cast<uint4 *>(out + ((size_t)c * T + t) * N + n) = y;
+        }
+    }
+}
+
 cudaError_t launch_corner_turn(const void *in, int in_dtype, void *out, int out_dtype, int N, int C, int T,
                                const int *d_perm, cudaStream_t s)
 {
     if ((long long)N * C * T == 0) return cudaSuccess;
     dim3 grid((T + 31) / 32, (N + 31) / 32, C), block(32, 8);
+    if (in_dtype == out_dtype && dtype_sample_bytes(in_dtype) == 4 && T % 4 == 0 && N % 4 == 0 &&
+        ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        dim3 g4((T + 63) / 64, (N + 31) / 32, C);
+        k_corner4v<<<g4, 256, 0, s>>>((const uint32_t *)in, (uint32_t *)out, N, C, T, d_perm);
+        return cudaGetLastError();
+    }
     if (in_dtype == out_dtype) {
         switch (dtype_sample_bytes(in_dtype)) {
         case 8: k_corner<uint2, uint2, 0><<<grid, block, 0, s>>>((const uint2 *)in, (uint2 *)out, N, C, T, d_perm); break;

@@ -32,12 +32,12 @@ struct BatchArgs {
     unsigned *err;
 };
 
-__device__ __forceinline__ int job_of(const BatchArgs &a, long long u)
+__device__ __forceinline__ int job_of(const BatchJob *jobs, int n_jobs, long long u)
 {
-    int lo = 0, hi = a.n_jobs - 1;
+    int lo = 0, hi = n_jobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (a.jobs[mid].unit0 <= u) lo = mid;
+        if (jobs[mid].unit0 <= u) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -48,50 +48,67 @@ struct UnitPos {
 };
 
 // Walks this CTA's units (blockIdx.x, + gridDim.x, ...), decoding positions.
-// The current job's scalars stay in registers; `fresh` tells the caller that
-// the job changed on the last step (so it reloads its own per-job fields).
+// Within a job the position advances by the grid size in the mixed radix
+// (M tile, time tile, channel) with additions and carries (the divisions are
+// done once per job).  `fresh` tells the caller that the job changed on the
+// last step, so it reloads its own per-job fields.
 struct UnitWalk {
-    const BatchArgs *a;
-    long long u, unit0, end;
-    int j, mt, t_tiles;
+    const BatchJob *jobs;
+    long long u, end;
+    int j, mt, t_tiles, m, tt, c, dm, dtt, dc;
     bool fresh;
-    __device__ void begin(const BatchArgs &args)
+    __device__ void begin(const BatchJob *jobs_)
     {
-        a = &args;
+        jobs = jobs_;
         u = blockIdx.x;
         j = -1;
-        unit0 = end = 0;
-        mt = t_tiles = 1;
+        end = 0;
         fresh = false;
     }
-    __device__ bool next(UnitPos &p)
+    __device__ bool next(const BatchArgs &a, UnitPos &p)
     {
-        if (u >= a->total_units) return false;
+        if (u >= a.total_units) return false;
         fresh = false;
         if (j < 0 || u >= end) {
-            j = j < 0 ? job_of(*a, u) : j + 1;
-            while (u >= a->jobs[j].unit0 + a->jobs[j].units) ++j;
-            const BatchJob &J = a->jobs[j];
-            unit0 = J.unit0;
+            j = j < 0 ? job_of(jobs, a.n_jobs, u) : j + 1;
+            while (u >= jobs[j].unit0 + jobs[j].units) ++j;
+            const BatchJob &J = jobs[j];
             end = J.unit0 + J.units;
             mt = J.mt;
             t_tiles = J.t_tiles;
+            const int v = (int)(u - J.unit0);
+            m = v % mt;
+            const int r = v / mt;
+            tt = r % t_tiles;
+            c = r / t_tiles;
+            const int g = (int)gridDim.x;
+            dm = g % mt;
+            dtt = (g / mt) % t_tiles;
+            dc = (g / mt) / t_tiles;
             fresh = true;
         }
-        const int v = (int)(u - unit0);
         p.j = j;
-        p.m = v % mt;
-        const int r = v / mt;
-        p.tt = r % t_tiles;
-        p.c = r / t_tiles;
+        p.m = m;
+        p.tt = tt;
+        p.c = c;
         u += gridDim.x;
+        // advance to the next unit of this job (garbage past its end: the job
+        // then changes and the position is decoded afresh)
+        m += dm;
+        const int k1 = m >= mt;
+        m -= k1 ? mt : 0;
+        tt += dtt + k1;
+        const int k2 = tt >= t_tiles;
+        tt -= k2 ? t_tiles : 0;
+        c += dc + k2;
         return true;
     }
 };
 
 template <bool F8, int WIN>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, const __grid_constant__ BatchJob single)
 {
+    const BatchJob *jobs = a.jobs ? a.jobs : &single;   // a table, or one job passed by value
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -141,15 +158,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
             uint32_t cnt = 0, issued = 0;
             int st = 0;
             UnitWalk w;
-            w.begin(a);
+            w.begin(jobs);
             UnitPos p;
             bool ok = true;
             const CUtensorMap *xmap = nullptr, *wmap = nullptr;
-            int kbn = 0, ke = 0, t_shift = 0;
+            int kbn = 0, ke = 0, t_shift = 0, c_base = 0;
             const uint32_t bytes = 16384 + a.nt * 128;
-            while (ok && w.next(p)) {
+            while (ok && w.next(a, p)) {
                 if (w.fresh) {
-                    const BatchJob &J = a.jobs[p.j];
+                    const BatchJob &J = jobs[p.j];
                     xmap = &J.xmap;
                     wmap = &J.wmap;
                     prefetch_tensormap(xmap);
@@ -157,6 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
                     kbn = J.kb;
                     ke = J.ke;
                     t_shift = J.t_shift;
+                    c_base = J.c_base;
                 }
                 for (int kb = 0; kb < kbn; ++kb) {
                     if (!mbar_wait(b_empty + 8 * st, ((cnt >> st) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
@@ -167,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
                     issued |= 1u << st;
                     const uint32_t dst = sx + st * a.stage_bytes;
                     mbar_arrive_expect_tx(b_full + 8 * st, bytes);
-                    tma_load_3d(dst, wmap, b_full + 8 * st, kb * ke, p.m * kRowsPerMTile, p.c);
+                    tma_load_3d(dst, wmap, b_full + 8 * st, kb * ke, p.m * kRowsPerMTile, c_base + p.c);
                     // window 0 starts t_shift samples before the chunk: those rows
                     // (negative time coordinates) read as zeros
                     tma_load_3d(dst + 16384, xmap, b_full + 8 * st, kb * ke, p.tt * a.nt - t_shift, p.c);
@@ -185,14 +203,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
             uint32_t par = 0, tpar = 0;
             int st = 0, acc = 0;
             UnitWalk w;
-            w.begin(a);
+            w.begin(jobs);
             UnitPos p;
             bool ok = true;
             int kbn = 0, ks_last = 4;
             uint32_t idesc = 0;
-            while (ok && w.next(p)) {
+            while (ok && w.next(a, p)) {
                 if (w.fresh) {
-                    const BatchJob &J = a.jobs[p.j];
+                    const BatchJob &J = jobs[p.j];
                     kbn = J.kb;
                     ks_last = J.ks_last;
                     idesc = J.idesc;
@@ -246,20 +264,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         uint32_t tpar = 0, kt = 0;
         int acc = 0;
         UnitWalk w;
-        w.begin(a);
+        w.begin(jobs);
         UnitPos p;
-        TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, 0, 0, 0, 0, 0, nullptr, nullptr, nullptr};
-        while (w.next(p)) {
-            if (w.fresh) {
-                const BatchJob &J = a.jobs[p.j];
-                o.T = J.T;
-                o.T_o = J.T_o;
-                o.B = J.B;
+        // the epilogue's view of the current job: only what the power epilogue
+        // reads, so few registers stay live across the tile loop
+        struct EpiView {
+            int t_int, b_pad;
+            const float *wscale;
+        } o{a.t_int, 0, nullptr};
+        int n_beams = 0;
+        while (w.next(a, p)) {
+            if (w.fresh) {   // per-channel scales offset to the job's first channel
+                const BatchJob &J = jobs[p.j];
+                n_beams = J.B;
                 o.b_pad = J.b_pad;
-                o.c_total = J.C;
-                o.wscale = J.wscale;
-                o.wsig = J.wsig;
-                o.out = J.out;
+                o.wscale = J.wscale ? J.wscale + (size_t)J.c_base * J.b_pad : nullptr;
             }
             if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
             tpar ^= 1u << acc;
@@ -274,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
             if (!active) {
                 tile_release(tempty, lane);
             } else {
-                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < o.B, p.c,
+                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < n_beams, p.c,
                                     stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
             }
             ++kt;
@@ -284,20 +303,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a)
         // ------------------------------------------------------------ store warp
         uint32_t kt = 0;
         UnitWalk w;
-        w.begin(a);
+        w.begin(jobs);
         UnitPos p;
         TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, 0, 0, 0, 0, 0, nullptr, nullptr, nullptr};
-        while (w.next(p)) {
-            if (w.fresh) {
-                const BatchJob &J = a.jobs[p.j];
+        while (w.next(a, p)) {
+            if (w.fresh) {   // outputs offset to the job's first channel
+                const BatchJob &J = jobs[p.j];
                 o.T = J.T;
                 o.T_o = J.T_o;
                 o.B = J.B;
                 o.b_pad = J.b_pad;
-                o.c_total = J.C;
-                o.out = J.out;
-                o.acc_in = J.acc_in;
-                o.acc_out = J.acc_out;
+                o.c_total = J.c_total;
+                o.out = J.out + (size_t)J.c_base * J.T_o;
+                o.acc_in = J.acc_in ? J.acc_in + J.c_base : nullptr;
+                o.acc_out = J.acc_out ? J.acc_out + J.c_base : nullptr;
             }
             const uint32_t sb = kt % kStageDepth;
             if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
@@ -337,9 +356,9 @@ static cudaError_t batch_attr()
 }
 
 template <bool F8, int WIN>
-static cudaError_t batch_launch(const BatchArgs &ka, int grid, int smem, cudaStream_t s)
+static cudaError_t batch_launch(const BatchArgs &ka, const BatchJob &single, int grid, int smem, cudaStream_t s)
 {
-    k_tc_batch<F8, WIN><<<grid, kTcThreads, smem, s>>>(ka);
+    k_tc_batch<F8, WIN><<<grid, kTcThreads, smem, s>>>(ka, single);
     return cudaGetLastError();
 }
 
@@ -371,7 +390,7 @@ static int batch_win(int t_int)
     } while (0)
 
 #define BF_ATTR(F, W) batch_attr<F, W>()
-#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, grid, core.smem, s)
+#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, single, grid, core.smem, s)
 
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t)
 {
@@ -425,8 +444,10 @@ bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int til
 }
 
 bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, const void *x_mma, int T,
-                         float *out, int t_shift, const float *acc_in, float *acc_out)
+                         float *out, int t_shift, const float *acc_in, float *acc_out, int c_base, int c_count)
 {
+    if (c_count < 0) c_count = p->C - c_base;
+    if (c_base < 0 || c_count < 0 || c_base + c_count > p->C) return set_error(BF_ERR_ARG, "channel range");
     if (T < 0) return set_error(BF_ERR_ARG, "n_samp must be >= 0");
     if (t_shift < 0 || t_shift >= p->t_int) return set_error(BF_ERR_ARG, "carried samples must be in [0, T_int)");
     const WeightFormat &f = p->wf;
@@ -434,7 +455,9 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
     const int frame = t_shift + T;   // samples from the start of window 0
     const int T_o = frame / p->t_int;
     const int partial = (acc_out && frame % p->t_int) ? 1 : 0;
-    J->C = p->C;
+    J->C = c_count;
+    J->c_base = c_base;
+    J->c_total = p->C;
     J->t_tiles = ((T_o + partial) * p->t_int + core.nt - 1) / core.nt;
     J->mt = f.m_pad / kRowsPerMTile;
     J->kb = f.kb;
@@ -455,13 +478,13 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
     J->out = out;
     J->acc_in = t_shift > 0 ? acc_in : nullptr;
     J->acc_out = partial ? acc_out : nullptr;
-    J->units = (T_o + partial) > 0 ? (long long)J->C * J->t_tiles * J->mt : 0;
+    J->units = (T_o + partial) > 0 ? (long long)c_count * J->t_tiles * J->mt : 0;
     if (J->units > 0) {
         if (T == 0) {   // nothing to read: the carried sum passes straight through
             J->units = 0;
             return set_error(BF_ERR_ARG, "a chunk with no samples cannot continue a window");
         }
-        if (!encode_voltage_map(&J->xmap, x_mma, 2 * p->N, T, p->C, f.es, f.ke, core.nt))
+        if (!encode_voltage_map(&J->xmap, x_mma, 2 * p->N, T, c_count, f.es, f.ke, core.nt))
             return set_error(BF_ERR_ARG, "voltage tensor map rejected (pointer or row stride not 16-byte aligned?)");
         if (!encode_weight_map(&J->wmap, p->d_w, f.k_pad, f.m_pad, p->C, f.es, f.ke))
             return set_error(BF_ERR_CUDA, "weight tensor map rejected");
@@ -479,8 +502,8 @@ long long batch_index(BatchJob *jobs, int n)
     return u;
 }
 
-cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
-                              unsigned *d_err, cudaStream_t s)
+static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, const BatchJob &single, int n,
+                               long long total_units, unsigned *d_err, cudaStream_t s)
 {
     if (total_units == 0) return cudaSuccess;
     BatchArgs ka;
@@ -499,6 +522,20 @@ cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int
     cudaError_t e;
     BF_BATCH_DISPATCH(core, BF_LAUNCH);
     return e;
+}
+
+cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
+                              unsigned *d_err, cudaStream_t s)
+{
+    static const BatchJob unused{};
+    return core_launch(core, d_jobs, unused, n, total_units, d_err, s);
+}
+
+cudaError_t batch_core_launch_one(const BatchCore &core, const BatchJob &job, unsigned *d_err, cudaStream_t s)
+{
+    BatchJob j = job;
+    j.unit0 = 0;
+    return core_launch(core, nullptr, j, 1, j.units, d_err, s);
 }
 
 }  // namespace bfi

@@ -5,9 +5,14 @@
 // follow the beamformer in the transient pipeline of Section 3 (Table 3);
 // the paper names the stages without formulas.
 //
-// One warp per (beam, channel) row: the mean and the population variance are
-// accumulated in FP64 (lane-strided, then a fixed butterfly), so the z values
-// and the threshold decisions do not depend on the launch shape.
+// One warp per (beam, channel) row, three passes over the row (it stays in
+// L1 after the first): each lane sums its strided elements in FP32 (a few
+// terms), the lanes' partial sums are combined in FP64 by a fixed butterfly,
+// so the mean and the population variance (of the deviations from that mean)
+// carry FP64 accuracy to within a few FP32 roundings, and do not depend on
+// the launch shape; z is then formed in FP32 ((P - mu) * (1 / sigma)) and
+// compared with k in FP32.  GB300's FP64 rate is low, so FP64 is kept to the
+// per-row reductions.
 #include "bf_internal.h"
 
 namespace bfi {
@@ -26,20 +31,22 @@ __global__ void k_detect(const float *__restrict__ P, int rows, int n_win, float
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= rows) return;
     const float *p = P + row * n_win;
-    double s = 0.0;
-    for (int j = lane; j < n_win; j += 32) s += (double)p[j];
-    const double mu = warp_sum(s) / n_win;
-    double v = 0.0;
+    float s = 0.f;
+    for (int j = lane; j < n_win; j += 32) s += p[j];
+    const double mu = warp_sum((double)s) / n_win;
+    const float mu_f = (float)mu;
+    float v = 0.f;
     for (int j = lane; j < n_win; j += 32) {
-        const double d = (double)p[j] - mu;
-        v += d * d;
+        const float d = p[j] - mu_f;
+        v = fmaf(d, d, v);
     }
-    const double sd = sqrt(warp_sum(v) / n_win);
+    const double var = warp_sum((double)v) / n_win;
+    const float inv = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.f;
     const int b = (int)(row / n_chan), c = (int)(row % n_chan);
     for (int j = lane; j < n_win; j += 32) {
-        const double z = sd > 0.0 ? ((double)p[j] - mu) / sd : 0.0;
-        if (z_out) z_out[row * n_win + j] = (float)z;
-        if (z > (double)k_sigma) {
+        const float z = (p[j] - mu_f) * inv;
+        if (z_out) z_out[row * n_win + j] = z;
+        if (z > k_sigma) {
             const int k = atomicAdd(n_hits, 1);
             if (k < max_hits) {
                 hits[3 * k] = b;

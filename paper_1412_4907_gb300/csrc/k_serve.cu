@@ -1,10 +1,10 @@
 // Real-time serving loop: voltage chunks of several streams (sub-arrays or
 // observing configurations, one plan each) arrive on the host at any time;
-// a scheduler thread admits them into device memory as it frees up, groups
-// the admitted chunks into steps (at most one chunk per stream per step) and
-// runs each step as one batched tensor-core launch, with the host-to-device
-// copies of the next step overlapping the launch of the current one and the
-// powers copied back as soon as their step ends.  Weights (in the plans) and
+// a scheduler thread admits each one into device memory as soon as its block
+// fits (its host-to-device copy is enqueued at once, so the link stays busy
+// while earlier chunks compute), groups the admitted chunks into steps (at
+// most one chunk per stream per step) and runs each step as one batched
+// tensor-core launch, and copies the powers back as soon as their step ends.  Weights (in the plans) and
 // the open integration window of every stream stay resident on the device
 // between chunks, so a stream cut into chunks of any length integrates
 // exactly as the same samples in one piece (Section 2.1 power detection and
@@ -96,6 +96,7 @@ struct Request {
     double t_submit = 0, t_start = 0, t_done = 0;
     size_t off = 0, bytes = 0;      // arena block
     size_t in_bytes = 0, x_off = 0, out_off = 0;
+    cudaEvent_t ev_c0 = nullptr, ev_c1 = nullptr;   // its host-to-device copy
     int n_windows = 0;
     int status = BF_OK;
     int step = -1;
@@ -116,10 +117,11 @@ struct Slot {
     BatchJob *d_jobs = nullptr;
     unsigned *d_err = nullptr;
     unsigned *h_err = nullptr;    // pinned
-    cudaEvent_t ev_h0 = nullptr, ev_in = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
     std::vector<Request *> reqs;
+    std::vector<cudaEvent_t> copy_ev;   // the step's chunks' copy events (start, end, ...)
+    std::vector<size_t> copy_bytes;
     bool busy = false, done = false;
-    size_t in_bytes = 0;
     bf_server *owner = nullptr;
 };
 
@@ -140,7 +142,9 @@ struct bf_server {
     std::mutex mu;
     std::condition_variable cv;        // wakes the scheduler
     std::condition_variable cv_done;   // wakes pollers
-    std::deque<Request *> pending;
+    std::deque<Request *> pending;                 // submitted, not yet in device memory
+    std::vector<std::deque<Request *>> admitted;   // per stream: copy enqueued, not yet in a step
+    std::vector<cudaEvent_t> ev_pool;              // spare copy events
     std::deque<Request *> completed;
     long long next_id = 1, submitted = 0, n_completed = 0, steps = 0;
     int inflight = 0, max_jobs = 0;
@@ -179,65 +183,89 @@ static void CUDART_CB step_done(void *arg)
     s->cv_done.notify_all();
 }
 
-// Picks the chunks of the next step (called with the lock held): FIFO order,
-// at most one chunk per stream, a stream's chunks in submission order, each
-// admitted only if its arena block fits now.
-static std::vector<Request *> select_step(bf_server *s)
+// Arena bytes of a chunk: its voltages, their FP16 widening (8/4-bit
+// inputs) and room for every window it can complete (at most ceil(T / T_int),
+// whatever window the stream left open).
+static void chunk_layout(const Stream &st, Request *r)
 {
-    std::vector<Request *> pick;
-    std::vector<char> seen(s->streams.size(), 0);
+    const bf_plan *p = st.plan;
+    const size_t n_samp = (size_t)p->C * r->T * p->N;
+    const size_t in_b = round256(n_samp * st.sample_bytes);
+    const size_t ex_b = st.expand ? round256(n_samp * 4) : 0;
+    const size_t out_b = round256((size_t)p->B * p->C * ((r->T + p->t_int - 1) / p->t_int) * sizeof(float));
+    r->bytes = in_b + ex_b + out_b;
+    r->in_bytes = n_samp * st.sample_bytes;
+    r->x_off = st.expand ? in_b : 0;      // relative until admitted
+    r->out_off = in_b + ex_b;
+}
+
+// Admits pending chunks (lock held): FIFO order, a stream's chunks in order
+// (a chunk that does not fit holds back the rest of its stream, other
+// streams may pass), each as soon as its arena block fits.
+static std::vector<Request *> admit(bf_server *s)
+{
+    std::vector<Request *> got;
+    std::vector<char> blocked(s->streams.size(), 0);
     for (auto it = s->pending.begin(); it != s->pending.end();) {
         Request *r = *it;
-        if (seen[r->cfg]) {
+        if (blocked[r->cfg]) {
             ++it;
             continue;
         }
-        seen[r->cfg] = 1;   // later chunks of this stream wait for the next step
         Stream &st = s->streams[r->cfg];
-        const bf_plan *p = st.plan;
-        const int frame = st.carry + r->T;
-        const int n_win = frame / p->t_int;
-        const size_t n_samp = (size_t)p->C * r->T * p->N;
-        const size_t in_b = round256(n_samp * st.sample_bytes);
-        const size_t ex_b = st.expand ? round256(n_samp * 4) : 0;
-        const size_t out_b = round256((size_t)p->B * p->C * n_win * sizeof(float));
-        const size_t off = s->arena.alloc(in_b + ex_b + out_b);
+        chunk_layout(st, r);
+        const size_t off = s->arena.alloc(r->bytes);
         if (off == SIZE_MAX) {
-            ++it;   // no room now: this stream waits (order), others may go
+            blocked[r->cfg] = 1;
+            ++it;
             continue;
         }
         r->off = off;
-        r->bytes = in_b + ex_b + out_b;
-        r->in_bytes = n_samp * st.sample_bytes;
-        r->x_off = st.expand ? off + in_b : off;
-        r->out_off = off + in_b + ex_b;
-        r->n_windows = n_win;
-        pick.push_back(r);
+        r->x_off += off;
+        r->out_off += off;
+        got.push_back(r);
         it = s->pending.erase(it);
         --st.queued;
     }
+    return got;
+}
+
+// Picks the chunks of the next step (lock held): the oldest admitted chunk of
+// every stream, so a stream's chunks run in order in successive steps.
+static std::vector<Request *> select_step(bf_server *s)
+{
+    std::vector<Request *> pick;
+    for (auto &q : s->admitted)
+        if (!q.empty()) {
+            pick.push_back(q.front());
+            q.pop_front();
+        }
     return pick;
+}
+
+// Enqueues the host-to-device copies of newly admitted chunks (lock not held).
+static std::string launch_copies(bf_server *s, std::vector<Request *> &got)
+{
+    cudaError_t e;
+    for (Request *r : got) {
+        r->t_start = now_s();
+        if ((e = cudaEventRecord(r->ev_c0, s->s_in)) != cudaSuccess ||
+            (r->in_bytes && (e = cudaMemcpyAsync(s->arena_base + r->off, r->hx, r->in_bytes, cudaMemcpyHostToDevice,
+                                                 s->s_in)) != cudaSuccess) ||
+            (e = cudaEventRecord(r->ev_c1, s->s_in)) != cudaSuccess)
+            return std::string("chunk copy: ") + cudaGetErrorString(e);
+    }
+    return "";
 }
 
 // Enqueues one step (lock not held).  Returns an error message or "".
 static std::string launch_step(bf_server *s, Slot &sl)
 {
     cudaError_t e;
-    const double t0 = now_s();
-    if ((e = cudaEventRecord(sl.ev_h0, s->s_in)) != cudaSuccess)
-        return std::string("step ordering: ") + cudaGetErrorString(e);
-    sl.in_bytes = 0;
-    for (Request *r : sl.reqs) {
-        r->t_start = t0;
-        sl.in_bytes += r->in_bytes;
-        if (r->in_bytes) {
-            e = cudaMemcpyAsync(s->arena_base + r->off, r->hx, r->in_bytes, cudaMemcpyHostToDevice, s->s_in);
-            if (e != cudaSuccess) return std::string("chunk copy: ") + cudaGetErrorString(e);
-        }
-    }
-    if ((e = cudaEventRecord(sl.ev_in, s->s_in)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(s->s_k, sl.ev_in, 0)) != cudaSuccess ||
-        (e = cudaMemsetAsync(sl.d_err, 0, sizeof(unsigned), s->s_k)) != cudaSuccess)
+    for (Request *r : sl.reqs)
+        if ((e = cudaStreamWaitEvent(s->s_k, r->ev_c1, 0)) != cudaSuccess)
+            return std::string("step ordering: ") + cudaGetErrorString(e);
+    if ((e = cudaMemsetAsync(sl.d_err, 0, sizeof(unsigned), s->s_k)) != cudaSuccess)
         return std::string("step ordering: ") + cudaGetErrorString(e);
     int n = 0;
     for (Request *r : sl.reqs) {
@@ -251,6 +279,7 @@ static std::string launch_step(bf_server *s, Slot &sl)
         // carried window: read acc[cur], leave the new open window in acc[1 - cur]
         const int frame = st.carry + r->T;
         const int rem = frame % p->t_int;
+        r->n_windows = frame / p->t_int;
         bf_status bs = batch_fill_job(s->core, &sl.h_jobs[n], p, s->arena_base + r->x_off, r->T,
                                       (float *)(s->arena_base + r->out_off), st.carry, st.acc[st.cur],
                                       st.acc[1 - st.cur]);
@@ -293,29 +322,92 @@ static void fail_requests(bf_server *s, std::vector<Request *> &reqs, int status
     reqs.clear();
 }
 
+static cudaEvent_t take_event(bf_server *s)
+{
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static bool all_admitted_empty(const bf_server *s)
+{
+    for (const auto &q : s->admitted)
+        if (!q.empty()) return false;
+    return true;
+}
+
+// Fails every chunk not yet in a step (lock held): after a CUDA error the
+// server serves nothing more.
+static void fail_queued(bf_server *s)
+{
+    std::vector<Request *> rest(s->pending.begin(), s->pending.end());
+    s->pending.clear();
+    for (auto &q : s->admitted) {
+        for (Request *r : q) {
+            s->arena.release(r->off, r->bytes);
+            rest.push_back(r);
+        }
+        q.clear();
+    }
+    fail_requests(s, rest, BF_ERR_CUDA);
+    s->cv_done.notify_all();
+}
+
 static void scheduler(bf_server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
-        // retire finished steps: kernel time from the events
+        // retire finished steps: kernel and copy times from the events
         for (Slot &sl : s->slots) {
             if (!sl.busy || !sl.done) continue;
-            float ms = 0.f, ms_in = 0.f;
+            float ms = 0.f;
+            double copy_ms = 0.0;
             lock.unlock();
-            const cudaError_t e = cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k1);
-            const cudaError_t e2 = cudaEventElapsedTime(&ms_in, sl.ev_h0, sl.ev_in);
-            lock.lock();
-            if (e == cudaSuccess) s->kernel_ms += ms;
-            if (e2 == cudaSuccess) {
-                s->copy_in_ms += ms_in;
-                s->copy_in_bytes += (double)sl.in_bytes;
+            const bool ok_k = cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k1) == cudaSuccess;
+            for (size_t i = 0; i + 1 < sl.copy_ev.size(); i += 2) {
+                float c = 0.f;
+                if (cudaEventElapsedTime(&c, sl.copy_ev[i], sl.copy_ev[i + 1]) == cudaSuccess) copy_ms += c;
             }
+            lock.lock();
+            if (ok_k) s->kernel_ms += ms;
+            s->copy_in_ms += copy_ms;
+            for (size_t b : sl.copy_bytes) s->copy_in_bytes += (double)b;
+            s->ev_pool.insert(s->ev_pool.end(), sl.copy_ev.begin(), sl.copy_ev.end());
+            sl.copy_ev.clear();
+            sl.copy_bytes.clear();
             sl.busy = sl.done = false;
             sl.reqs.clear();
             --s->inflight;
         }
-        if (s->stop && s->pending.empty() && s->inflight == 0) break;
+        if (s->stop && s->pending.empty() && all_admitted_empty(s) && s->inflight == 0) break;
+        const bool go = s->fault.empty() && (!s->paused || s->stop);
+        // admission: copies start as soon as a chunk's block fits
+        std::vector<Request *> got;
+        if (go && !s->pending.empty()) got = admit(s);
+        if (!got.empty()) {
+            for (Request *r : got) {
+                r->ev_c0 = take_event(s);
+                r->ev_c1 = take_event(s);
+            }
+            lock.unlock();
+            const std::string err = launch_copies(s, got);
+            lock.lock();
+            if (!err.empty()) {
+                if (s->fault.empty()) s->fault = err;
+                for (Request *r : got) s->arena.release(r->off, r->bytes);
+                fail_requests(s, got, BF_ERR_CUDA);
+                fail_queued(s);
+                continue;
+            }
+            for (Request *r : got) s->admitted[r->cfg].push_back(r);
+        }
+        // a step: the oldest admitted chunk of every stream
         Slot *free_slot = nullptr;
         for (Slot &sl : s->slots)
             if (!sl.busy) {
@@ -323,22 +415,24 @@ static void scheduler(bf_server *s)
                 break;
             }
         std::vector<Request *> pick;
-        if (free_slot && !s->pending.empty() && s->fault.empty() && (!s->paused || s->stop)) pick = select_step(s);
+        if (free_slot && go) pick = select_step(s);
         if (pick.empty()) {
-            if (!s->fault.empty() && !s->pending.empty()) {   // a broken stream serves nothing more
-                std::vector<Request *> rest(s->pending.begin(), s->pending.end());
-                s->pending.clear();
-                fail_requests(s, rest, BF_ERR_CUDA);
-                s->cv_done.notify_all();
+            if (!s->fault.empty() && (!s->pending.empty() || !all_admitted_empty(s))) {
+                fail_queued(s);
                 continue;
             }
-            s->cv.wait_for(lock, std::chrono::milliseconds(50));
+            if (got.empty()) s->cv.wait_for(lock, std::chrono::milliseconds(50));
             continue;
         }
         free_slot->busy = true;
         free_slot->done = false;
         free_slot->reqs = pick;
-        for (Request *r : pick) r->step = (int)s->steps;
+        for (Request *r : pick) {
+            r->step = (int)s->steps;
+            free_slot->copy_ev.push_back(r->ev_c0);
+            free_slot->copy_ev.push_back(r->ev_c1);
+            free_slot->copy_bytes.push_back(r->in_bytes);
+        }
         ++s->steps;
         ++s->inflight;
         s->max_jobs = std::max(s->max_jobs, (int)pick.size());
@@ -384,11 +478,10 @@ static void server_free(bf_server *s)
         if (sl.d_jobs) cudaFree(sl.d_jobs);
         if (sl.d_err) cudaFree(sl.d_err);
         if (sl.h_err) cudaFreeHost(sl.h_err);
-        if (sl.ev_h0) cudaEventDestroy(sl.ev_h0);
-        if (sl.ev_in) cudaEventDestroy(sl.ev_in);
         if (sl.ev_k0) cudaEventDestroy(sl.ev_k0);
         if (sl.ev_k1) cudaEventDestroy(sl.ev_k1);
     }
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     for (Stream &st : s->streams)
         for (float *a : st.acc)
             if (a) cudaFree(a);
@@ -425,6 +518,7 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
     s->core = core;
     s->device = plans[0]->device;
     s->streams.resize(n_configs);
+    s->admitted.resize(n_configs);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < n_configs && e == cudaSuccess; ++i) {
         Stream &q = s->streams[i];
@@ -448,7 +542,6 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
             (e = cudaMalloc((void **)&sl.d_jobs, sizeof(BatchJob) * n_configs)) == cudaSuccess &&
             (e = cudaMalloc((void **)&sl.d_err, sizeof(unsigned))) == cudaSuccess &&
             (e = cudaHostAlloc((void **)&sl.h_err, sizeof(unsigned), cudaHostAllocDefault)) == cudaSuccess &&
-            (e = cudaEventCreate(&sl.ev_h0)) == cudaSuccess && (e = cudaEventCreate(&sl.ev_in)) == cudaSuccess &&
             (e = cudaEventCreate(&sl.ev_k0)) == cudaSuccess)
             e = cudaEventCreate(&sl.ev_k1);
         if (e == cudaSuccess) *sl.h_err = 0;

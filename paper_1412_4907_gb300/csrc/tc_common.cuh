@@ -118,24 +118,17 @@ __device__ __forceinline__ void epi_power_tile(const O &o, uint32_t taddr, int c
         }
     };
     int col = 0;
-    if (WIN > 0 && cols == 64) {
-        uint32_t r[64];
-        tmem_ld64r(taddr, r);
-        tile_release(b_tempty_acc, lane);
-#pragma unroll
-        for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
-            emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
-        col = 64;
-    } else if (WIN > 0 && cols % 128 == 0) {
-        // 128 columns per load; the accumulator is released after the last
+    if (WIN > 0 && cols % 64 == 0) {
+        // 64 columns per load (64 registers, leaving room for the walker state
+        // of the batched kernel); the accumulator is released after the last
         // load, before the squares are summed
-        for (; col < cols; col += 128) {
-            uint32_t r[128];
-            tmem_ld128(taddr + col, r);
-            if (col + 128 == cols) tile_release(b_tempty_acc, lane);
+        for (; col < cols; col += 64) {
+            uint32_t r[64];
+            tmem_ld64r(taddr + col, r);
+            if (col + 64 == cols) tile_release(b_tempty_acc, lane);
 #pragma unroll
-            for (int k = 0; k < 128 / (WIN > 0 ? WIN : 128); ++k)
-                emit(sumsq_pk<(WIN > 0 ? WIN : 128)>(r + k * (WIN > 0 ? WIN : 128)));
+            for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
+                emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
         }
     }
     const int n64 = (cols - col) / 64, rem = (cols - col) % 64;   // rem is a multiple of 16

@@ -31,10 +31,14 @@ def test_detect_matches_oracle(bf, B, C, W):
     torch.cuda.synchronize()
     z_ref, hits_ref = oracle.detect(P, k)
     assert np.max(np.abs(z.cpu().numpy() - z_ref)) <= 1e-5 * max(1.0, np.max(np.abs(z_ref)))
-    # decisions within 1e-6 of the threshold could go either way in FP64 order; none here
-    assert np.min(np.abs(z_ref - k)) > 1e-6
-    got = sorted(map(tuple, hits.cpu().numpy().tolist()))
-    assert total == len(hits_ref) and got == sorted(map(tuple, hits_ref.tolist()))
+    # z is formed in FP32 on the GPU: a decision within 1e-4 of the threshold may
+    # go either way; every other decision must match the FP64 oracle's
+    near = {tuple(ix) for ix in np.argwhere(np.abs(z_ref - k) <= 1e-4).tolist()}
+    got = {tuple(h) for h in hits.cpu().numpy().tolist()}
+    ref = {tuple(h) for h in hits_ref.tolist()}
+    assert total == len(got)
+    assert got - near == ref - near
+    assert len(near) <= 3
 
 
 def test_detect_overflow_and_empty(bf):
