@@ -851,7 +851,7 @@ def main():
                     help="serving stream of 6 configurations with Poisson arrivals (p50/p99 latency)")
     ap.add_argument("--serve-rate", type=float, default=400.0, help="chunk arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="seconds of arrivals")
-    ap.add_argument("--serve-mem", type=float, default=48.0, help="server arena in GiB")
+    ap.add_argument("--serve-mem", type=float, default=96.0, help="server arena in GiB")
     ap.add_argument("--serve-steps", type=int, default=3, help="server steps in flight (1..8)")
     ap.add_argument("--serve-fp32-chunks", type=int, default=40, help="chunks for the FP32 single-job comparison")
     ap.add_argument("--channels", type=int, default=0,

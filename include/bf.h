@@ -368,7 +368,7 @@ typedef struct bf_server_counters {
 
 /*
  * bf_server_create — server over plans[0 .. n_configs-1] (host array, read
- * during the call).  mem_bytes: device arena for admitted chunks (voltages,
+ * during the call; at most 16 streams).  mem_bytes: device arena for admitted chunks (voltages,
  * FP16 widening of integer inputs, powers); a chunk waits until its block
  * fits.  max_steps (1..8): steps in flight at once.  tile_t as
  * bf_batch_create.  Waits for the plans' weights, allocates the arena and

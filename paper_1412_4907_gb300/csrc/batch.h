@@ -61,9 +61,19 @@ long long batch_index(BatchJob *jobs, int n);
 cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
                               unsigned *d_err, cudaStream_t s);
 
-// One persistent launch of a single job passed by value (kernel parameter
-// space): no table copy, so it is stream-ordered and capturable like any
-// launch.  Used by the single-plan path for large antenna counts.
+// Jobs a launch can take by value in its parameters (16 x 384 bytes, within
+// the 32 KB parameter space of current CUDA): no table copy, so nothing of the
+// launch waits behind other host-to-device copies.
+constexpr int kParamJobs = 16;
+struct ParamJobs {
+    BatchJob j[kParamJobs];
+};
+
+// One persistent launch over jobs[0 .. n-1] (n <= kParamJobs) passed by
+// value.  Used by single plans with large antenna counts (n = 1), the serving
+// loop and small batches.
+cudaError_t batch_core_launch_params(const BatchCore &core, const BatchJob *jobs, int n, long long total_units,
+                                     unsigned *d_err, cudaStream_t s);
 cudaError_t batch_core_launch_one(const BatchCore &core, const BatchJob &job, unsigned *d_err, cudaStream_t s);
 
 }  // namespace bfi

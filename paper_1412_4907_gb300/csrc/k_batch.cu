@@ -106,9 +106,9 @@ struct UnitWalk {
 };
 
 template <bool F8, int WIN>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, const __grid_constant__ BatchJob single)
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, const __grid_constant__ ParamJobs pj)
 {
-    const BatchJob *jobs = a.jobs ? a.jobs : &single;   // a table, or one job passed by value
+    const BatchJob *jobs = a.jobs ? a.jobs : pj.j;   // a table in device memory, or jobs passed by value
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -356,9 +356,9 @@ static cudaError_t batch_attr()
 }
 
 template <bool F8, int WIN>
-static cudaError_t batch_launch(const BatchArgs &ka, const BatchJob &single, int grid, int smem, cudaStream_t s)
+static cudaError_t batch_launch(const BatchArgs &ka, const ParamJobs &pj, int grid, int smem, cudaStream_t s)
 {
-    k_tc_batch<F8, WIN><<<grid, kTcThreads, smem, s>>>(ka, single);
+    k_tc_batch<F8, WIN><<<grid, kTcThreads, smem, s>>>(ka, pj);
     return cudaGetLastError();
 }
 
@@ -390,7 +390,7 @@ static int batch_win(int t_int)
     } while (0)
 
 #define BF_ATTR(F, W) batch_attr<F, W>()
-#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, single, grid, core.smem, s)
+#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, pj, grid, core.smem, s)
 
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t)
 {
@@ -502,7 +502,7 @@ long long batch_index(BatchJob *jobs, int n)
     return u;
 }
 
-static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, const BatchJob &single, int n,
+static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, const ParamJobs &pj, int n,
                                long long total_units, unsigned *d_err, cudaStream_t s)
 {
     if (total_units == 0) return cudaSuccess;
@@ -527,15 +527,24 @@ static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, co
 cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
                               unsigned *d_err, cudaStream_t s)
 {
-    static const BatchJob unused{};
+    static const ParamJobs unused{};
     return core_launch(core, d_jobs, unused, n, total_units, d_err, s);
+}
+
+cudaError_t batch_core_launch_params(const BatchCore &core, const BatchJob *jobs, int n, long long total_units,
+                                     unsigned *d_err, cudaStream_t s)
+{
+    if (n < 1 || n > kParamJobs) return cudaErrorInvalidValue;
+    ParamJobs pj;
+    memcpy((void *)pj.j, (const void *)jobs, sizeof(BatchJob) * n);
+    return core_launch(core, nullptr, pj, n, total_units, d_err, s);
 }
 
 cudaError_t batch_core_launch_one(const BatchCore &core, const BatchJob &job, unsigned *d_err, cudaStream_t s)
 {
     BatchJob j = job;
     j.unit0 = 0;
-    return core_launch(core, nullptr, j, 1, j.units, d_err, s);
+    return batch_core_launch_params(core, &j, 1, j.units, d_err, s);
 }
 
 }  // namespace bfi
@@ -680,9 +689,13 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
             if (e != cudaSuccess) return cuda_error(e, "integer expansion");
         }
     }
-    e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * b->n, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_error(e, "batch table upload");
-    e = batch_core_launch(b->core, b->d_jobs, b->n, b->total_units, b->d_err, s);
+    if (b->n <= kParamJobs) {
+        e = batch_core_launch_params(b->core, b->h_jobs, b->n, b->total_units, b->d_err, s);
+    } else {
+        e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * b->n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_error(e, "batch table upload");
+        e = batch_core_launch(b->core, b->d_jobs, b->n, b->total_units, b->d_err, s);
+    }
     if (e != cudaSuccess) return cuda_error(e, "batched tensor-core kernel");
     return BF_OK;
 }

@@ -113,8 +113,7 @@ struct Stream {   // one configuration: its plan and its open window
 };
 
 struct Slot {
-    BatchJob *h_jobs = nullptr;   // pinned
-    BatchJob *d_jobs = nullptr;
+    BatchJob *h_jobs = nullptr;   // the step's job table (passed in the launch parameters)
     unsigned *d_err = nullptr;
     unsigned *h_err = nullptr;    // pinned
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
@@ -199,16 +198,25 @@ static void chunk_layout(const Stream &st, Request *r)
     r->out_off = in_b + ex_b;
 }
 
+// Chunks of one stream admitted ahead of its steps.  Steps take one chunk
+// per stream, so admitting more would only lengthen the copy queue (and the
+// wait of every later chunk behind it) without raising throughput.
+constexpr size_t kAdmitAhead = 2;
+
 // Admits pending chunks (lock held): FIFO order, a stream's chunks in order
 // (a chunk that does not fit holds back the rest of its stream, other
-// streams may pass), each as soon as its arena block fits.
+// streams may pass), each as soon as its arena block fits and its stream has
+// fewer than kAdmitAhead chunks waiting for a step.
 static std::vector<Request *> admit(bf_server *s)
 {
     std::vector<Request *> got;
     std::vector<char> blocked(s->streams.size(), 0);
+    std::vector<size_t> ahead(s->streams.size());
+    for (size_t i = 0; i < ahead.size(); ++i) ahead[i] = s->admitted[i].size();
     for (auto it = s->pending.begin(); it != s->pending.end();) {
         Request *r = *it;
-        if (blocked[r->cfg]) {
+        if (blocked[r->cfg] || ahead[r->cfg] >= kAdmitAhead) {
+            blocked[r->cfg] = 1;
             ++it;
             continue;
         }
@@ -223,6 +231,7 @@ static std::vector<Request *> admit(bf_server *s)
         r->off = off;
         r->x_off += off;
         r->out_off += off;
+        ++ahead[r->cfg];
         got.push_back(r);
         it = s->pending.erase(it);
         --st.queued;
@@ -289,10 +298,12 @@ static std::string launch_step(bf_server *s, Slot &sl)
         ++n;
     }
     const long long units = batch_index(sl.h_jobs, n);
-    if ((e = cudaMemcpyAsync(sl.d_jobs, sl.h_jobs, sizeof(BatchJob) * n, cudaMemcpyHostToDevice, s->s_k)) !=
-            cudaSuccess ||
-        (e = cudaEventRecord(sl.ev_k0, s->s_k)) != cudaSuccess ||
-        (e = batch_core_launch(s->core, sl.d_jobs, n, units, sl.d_err, s->s_k)) != cudaSuccess ||
+    // the job table travels in the launch parameters: a table copy here would
+    // sit in the host-to-device queue behind the chunks admitted for later
+    // steps and hold this launch back
+    if ((e = cudaEventRecord(sl.ev_k0, s->s_k)) != cudaSuccess ||
+        (e = n <= kParamJobs ? batch_core_launch_params(s->core, sl.h_jobs, n, units, sl.d_err, s->s_k)
+                             : cudaErrorInvalidValue) != cudaSuccess ||
         (e = cudaEventRecord(sl.ev_k1, s->s_k)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s->s_out, sl.ev_k1, 0)) != cudaSuccess)
         return std::string("step launch: ") + cudaGetErrorString(e);
@@ -475,7 +486,6 @@ static void server_free(bf_server *s)
     if (s->s_out) cudaStreamSynchronize(s->s_out);
     for (Slot &sl : s->slots) {
         if (sl.h_jobs) cudaFreeHost(sl.h_jobs);
-        if (sl.d_jobs) cudaFree(sl.d_jobs);
         if (sl.d_err) cudaFree(sl.d_err);
         if (sl.h_err) cudaFreeHost(sl.h_err);
         if (sl.ev_k0) cudaEventDestroy(sl.ev_k0);
@@ -506,6 +516,8 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
     *out = nullptr;
     if (max_steps < 1 || max_steps > 8) return set_error(BF_ERR_ARG, "max_steps must be in 1..8");
     if (mem_bytes < 4096) return set_error(BF_ERR_ARG, "memory budget too small");
+    if (n_configs > kParamJobs)
+        return set_error(BF_ERR_UNSUPPORTED, "a server takes at most " + std::to_string(kParamJobs) + " streams");
     BatchCore core;
     bf_status st = batch_core_init(&core, plans, n_configs, tile_t);
     if (st != BF_OK) return st;
@@ -539,7 +551,6 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
         sl.owner = s;
         if ((e = cudaHostAlloc((void **)&sl.h_jobs, sizeof(BatchJob) * n_configs, cudaHostAllocDefault)) ==
                 cudaSuccess &&
-            (e = cudaMalloc((void **)&sl.d_jobs, sizeof(BatchJob) * n_configs)) == cudaSuccess &&
             (e = cudaMalloc((void **)&sl.d_err, sizeof(unsigned))) == cudaSuccess &&
             (e = cudaHostAlloc((void **)&sl.h_err, sizeof(unsigned), cudaHostAllocDefault)) == cudaSuccess &&
             (e = cudaEventCreate(&sl.ev_k0)) == cudaSuccess)
