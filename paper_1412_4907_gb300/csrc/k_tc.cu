@@ -20,15 +20,21 @@
 //                128 x NT x 16 (or x32 for FP8) per instruction, into two
 //                NT-column FP32 accumulators (the epilogue drains one while
 //                the next tile accumulates)
-//   warps 2-9    epilogue, two warps per TMEM lane quarter, each on a half
-//                of the tile's columns: the half is read with 128-column
-//                tcgen05.ld and the accumulator handed back to the MMA before
-//                any arithmetic; then squares with packed FP32 FMAs, window
-//                sums in a fixed order, re+im combination via one shuffle (the
-//                two rows of a beam are 16 lanes apart), window powers staged
-//                in shared memory
-//   warp 10      store warp: writes each staged tile as one run of windows
+//   warps 2-17   epilogue in two groups of 8 that take alternate tiles (and
+//                so alternate accumulators): while one group reads and sums a
+//                tile the other is already waiting for the next, so the
+//                accumulator's read-out and the squaring no longer sit in
+//                series with the MMA of the tile after next.  In a group, two
+//                warps per TMEM lane quarter, each on a half of the tile's
+//                columns, read with 64-column tcgen05.ld; the accumulator is
+//                handed back to the MMA before any arithmetic; then squares
+//                with packed FP32 FMAs, window sums in a fixed order, re+im
+//                combination via one shuffle (the two rows of a beam are 16
+//                lanes apart), window powers staged in shared memory
+//   warp 18      store warp: writes each staged tile as one run of windows
 //                per beam (16-byte stores), four tiles in flight.
+// 19 warps: at most 96 registers a thread (five warps share an SM
+// sub-partition's 16K registers).
 // Work: the M tiles of a channel are split into weight groups; the CTAs are
 // arranged as P sets of Gq CTAs, the CTAs of one set hold different groups
 // and walk the same (channel, time-tile) range in step, so a voltage tile is
@@ -48,7 +54,7 @@
 
 namespace bfi {
 
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;               // two groups of 8, taking alternate tiles
 constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
 constexpr int kTcThreads = (3 + kEpiWarps) * 32;
 constexpr int kStageDepth = 4;                     // staged tiles in flight
@@ -140,7 +146,7 @@ __device__ __forceinline__ float sumsq_pk(const uint32_t *r)
 // STREAM: weights are not resident; every pipeline stage carries one 64-column
 // K block of the weight tile and of the voltage tile (large antenna counts).
 template <bool F8, int WIN, bool COMPLEX, bool STREAM>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __maxnreg__(96)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int i = 0; i < a.nacc; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
-            mbar_init(b_tempty + 8 * i, kEpiWarps);
+            mbar_init(b_tempty + 8 * i, kEpiWarps / 2);   // one group releases each use
         }
         mbar_init(b_drain, 1);
         for (int s = 0; s < a.gmax; ++s) {
@@ -401,8 +407,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (warp < kStoreWarp) {
         // -------------------------------------------------------------- epilogue
         const int e = warp - 2;
+        const int grp = e >> 3;               // this group takes the tiles with kt % 2 == grp
         const int q = warp & 3;               // TMEM lane quarter this warp may access
-        const int h = e >> 2;                 // column slice
+        const int h = (e & 7) >> 2;           // column slice
         const int part = (lane >> 4) & 1;     // 0: re row, 1: im row
         const int bq = q * 16 + (lane & 15);  // beam within the M tile
         const int cols = a.nt / a.nsplit;
@@ -419,6 +426,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (long long ct = ct0; ct < ct1 && ok; ++ct) {
                 const int cg = a.c_base + c;
                 for (int s = 0; s < gs; ++s, ++kt) {
+                    if ((int)(kt & 1u) != grp) {   // the other group's tile
+                        if (++acc == a.nacc) acc = 0;
+                        continue;
+                    }
                     if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
                         break;
@@ -503,24 +514,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             }
                         };
                         int col = 0;
-                        if (WIN > 0 && cols == 64) {
-                            uint32_t r[64];
-                            tmem_ld64r(taddr, r);
-                            release();
+                        if (WIN > 0 && cols % 64 == 0) {
+                            for (; col < cols; col += 64) {
+                                uint32_t r[64];
+                                tmem_ld64r(taddr + col, r);
+                                if (col + 64 == cols) release();
 #pragma unroll
-                            for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
-                                emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
-                            col = 64;
-                        } else if (WIN > 0 && cols % 128 == 0) {
-                            // 128 columns per load; the accumulator is released after the
-                            // last load, before the squares are summed
-                            for (; col < cols; col += 128) {
-                                uint32_t r[128];
-                                tmem_ld128(taddr + col, r);
-                                if (col + 128 == cols) release();
-#pragma unroll
-                                for (int k = 0; k < 128 / (WIN > 0 ? WIN : 128); ++k)
-                                    emit(sumsq_pk<(WIN > 0 ? WIN : 128)>(r + k * (WIN > 0 ? WIN : 128)));
+                                for (int k = 0; k < 64 / (WIN > 0 ? WIN : 64); ++k)
+                                    emit(sumsq_pk<(WIN > 0 ? WIN : 64)>(r + k * (WIN > 0 ? WIN : 64)));
                             }
                         }
                         const int n64 = (cols - col) / 64, rem = (cols - col) % 64;   // rem is a multiple of 16
@@ -781,7 +782,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.nsplit = cfg.nsplit;
     ka.wpt = cfg.nt / ta.t_int;
     ka.xst = cfg.xst;
-    ka.nacc = std::min(kMaxAcc, kTmemCols / cfg.nt);
+    ka.nacc = std::min(kMaxAcc, kTmemCols / cfg.nt) & ~1;   // even: each group keeps its own accumulators
     ka.c_base = ta.c_base;
     ka.c_total = ta.c_total;
     ka.T = ta.T;
