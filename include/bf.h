@@ -423,8 +423,8 @@ double bf_server_now(void);
  * Table 3: detrending and thresholding; the paper gives no formulas, so this
  * is the library's reading): for every beam b and channel c over the n_win
  * windows of d_power [B][C][n_win] (device, float),
- *   mu = mean_j P,  sigma = sqrt(mean_j (P - mu)^2)   (per-row sums in FP64),
- *   z[b][c][j] = (P - mu) / sigma   (FP32; 0 where sigma = 0),
+ *   mu = mean_j P,  sigma = sqrt(mean_j (P - mu)^2)   (FP32, two passes,
+ *   fixed reduction order),  z[b][c][j] = (P - mu) / sigma   (0 where sigma = 0),
  * written to d_z (device, float [B][C][n_win], or NULL), and every (b, c, j)
  * with z > k_sigma appended to d_hits (device, int [max_hits][3], in no
  * particular order); *d_n_hits (device int) receives the number of hits,

@@ -289,7 +289,9 @@ static bf_status run_range(bf_plan *p, const void *x, int c_base, int c_launch, 
 {
     const int T_o = T / p->t_int;
     if (mode == 2) {   // incoherent
-        BF_CUDA(launch_incoherent(x, p->dtype, p->layout, p->d_mask, p->N, c_launch, T, p->t_int,
+        // an all-ones mask is passed as none (the kernel's unmasked paths are faster)
+        const bool masked = std::find(p->mask.begin(), p->mask.end(), (uint8_t)0) != p->mask.end();
+        BF_CUDA(launch_incoherent(x, p->dtype, p->layout, masked ? p->d_mask : nullptr, p->N, c_launch, T, p->t_int,
                                   out + (size_t)c_base * T_o, s),
                 "incoherent kernel");
         return BF_OK;

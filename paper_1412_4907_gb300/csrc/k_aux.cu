@@ -123,6 +123,41 @@ __global__ void k_corner4v(const uint32_t *__restrict__ in, uint32_t *__restrict
     }
 }
 
+// 4-byte samples with any T: 32 antennas x 128 samples per block, 4-byte
+// loads (a warp reads 128 contiguous bytes of one antenna row) and 16-byte
+// stores (4 antennas of one sample); needs N % 4 == 0 and a 16-byte aligned
+// output.  16 loads per thread in flight.
+__global__ void k_corner4s(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int N, int C, int T,
+                           const int *__restrict__ perm)
+{
+    __shared__ uint32_t tile[32][129];   // [antenna][sample], padded
+    const int t0 = blockIdx.x * 128, n0 = blockIdx.y * 32, c = blockIdx.z;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;   // 8 warps
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int idx = wid * 16 + k;         // 128 (antenna, 32-sample segment) pairs
+        const int j = idx >> 2, seg = idx & 3;
+        const int n = n0 + j, t = t0 + seg * 32 + lane;
+        if (n < N && t < T) {
+            const int src = perm ? perm[n] : n;
+            tile[j][seg * 32 + lane] = in[((size_t)src * C + c) * T + t];
+        }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < 1024; v += blockDim.x) {
+        const int i = v >> 3, q = v & 7;      // sample t0 + i, antennas 4q .. 4q+3
+        const int t = t0 + i, n = n0 + 4 * q;
+        if (t < T && n < N) {                 // N % 4 == 0
+            uint4 y;
+            y.x = tile[4 * q][i];
+            y.y = tile[4 * q + 1][i];
+            y.z = tile[4 * q + 2][i];
+            y.w = tile[4 * q + 3][i];
+            *reinterpret_cast<uint4 *>(out + ((size_t)c * T + t) * N + n) = y;
+        }
+    }
+}
+
 cudaError_t launch_corner_turn(const void *in, int in_dtype, void *out, int out_dtype, int N, int C, int T,
                                const int *d_perm, cudaStream_t s)
 {
@@ -132,6 +167,11 @@ cudaError_t launch_corner_turn(const void *in, int in_dtype, void *out, int out_
         ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
         dim3 g4((T + 63) / 64, (N + 31) / 32, C);
         k_corner4v<<<g4, 256, 0, s>>>((const uint32_t *)in, (uint32_t *)out, N, C, T, d_perm);
+        return cudaGetLastError();
+    }
+    if (in_dtype == out_dtype && dtype_sample_bytes(in_dtype) == 4 && N % 4 == 0 && ((uintptr_t)out & 15) == 0) {
+        dim3 g4((T + 127) / 128, (N + 31) / 32, C);
+        k_corner4s<<<g4, 256, 0, s>>>((const uint32_t *)in, (uint32_t *)out, N, C, T, d_perm);
         return cudaGetLastError();
     }
     if (in_dtype == out_dtype) {
@@ -220,27 +260,61 @@ template <int DT, bool NCT>
 __global__ void k_incoherent(const void *__restrict__ x, const uint8_t *__restrict__ mask, int N, int C, int T,
                              int t_int, int T_o, float *__restrict__ out)
 {
+    // one warp per (channel, window): the window's t_int x N samples, 32-bit
+    // index arithmetic (t_int * N < 2^31 is checked on the host), the antenna
+    // of each element tracked incrementally, two accumulators per lane
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wid >= (long long)C * T_o) return;
     const int c = (int)(wid / T_o), j = (int)(wid % T_o);
-    const long long n_el = (long long)t_int * N;
-    float s = 0.f;
-    for (long long i = lane; i < n_el; i += 32) {
-        int n, tt;
-        size_t idx;
-        if (NCT) {
-            n = (int)(i / t_int);
-            tt = (int)(i % t_int);
-            idx = ((size_t)n * C + c) * T + (size_t)j * t_int + tt;
-        } else {
-            n = (int)(i % N);
-            idx = ((size_t)c * T + (size_t)j * t_int) * N + i;
+    const int n_el = t_int * N;
+    float s0 = 0.f, s1 = 0.f;
+    if (NCT) {
+        // element i = n * t_int + tt: a warp reads consecutive samples of one antenna row
+        for (int i = lane; i < n_el; i += 32) {
+            const int n = i / t_int, tt = i - n * t_int;
+            if (mask && !mask[n]) continue;
+            const float2 v = load_sample<DT>(x, ((size_t)n * C + c) * T + (size_t)j * t_int + tt);
+            s0 = fmaf(v.x, v.x, s0);
+            s1 = fmaf(v.y, v.y, s1);
         }
-        if (mask && !mask[n]) continue;
-        float2 v = load_sample<DT>(x, idx);
-        s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
+    } else if ((DT == BF_C16F || DT == BF_C16BF) && !mask && (n_el & 3) == 0 && ((uintptr_t)x & 15) == 0 &&
+               ((((size_t)c * T + (size_t)j * t_int) * N) & 3) == 0) {
+        // 16-bit samples, no mask, aligned window: 16-byte loads of 4 samples
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(x) + (((size_t)c * T + (size_t)j * t_int) * N >> 2);
+        const int n4 = n_el >> 2;
+#pragma unroll 4
+        for (int i = lane; i < n4; i += 32) {
+            const uint4 q = w4[i];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float2 v;
+                if constexpr (DT == BF_C16F) {
+                    v = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+                } else {
+                    v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[k]));
+                }
+                s0 = fmaf(v.x, v.x, s0);
+                s1 = fmaf(v.y, v.y, s1);
+            }
+        }
+    } else {
+        // the window is contiguous: [t_int][N] samples from (c, j * t_int)
+        const size_t base = ((size_t)c * T + (size_t)j * t_int) * N;
+        int n = lane % N;
+        const int step = 32 % N;
+        for (int i = lane; i < n_el; i += 32) {
+            if (!mask || mask[n]) {
+                const float2 v = load_sample<DT>(x, base + i);
+                s0 = fmaf(v.x, v.x, s0);
+                s1 = fmaf(v.y, v.y, s1);
+            }
+            n += step;
+            if (n >= N) n -= N;
+        }
     }
+    float s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[(size_t)c * T_o + j] = s;
@@ -261,6 +335,7 @@ cudaError_t launch_incoherent(const void *x, int dtype, int layout, const uint8_
                               int t_int, float *out, cudaStream_t s)
 {
     if ((long long)C * (T / t_int) == 0) return cudaSuccess;
+    if ((long long)t_int * N >= (1ll << 31)) return cudaErrorInvalidValue;
     switch (dtype) {
     case BF_C32: inc_launch<BF_C32>(x, layout, d_mask, N, C, T, t_int, out, s); break;
     case BF_C16F: inc_launch<BF_C16F>(x, layout, d_mask, N, C, T, t_int, out, s); break;

@@ -309,7 +309,7 @@ def test_input_order_permutation(bf):
     check("tc_input_order_permuted", P1, P_ref, synth.C16F)
 
 
-@pytest.mark.parametrize("mode", [synth.C32, synth.C16F, synth.C8E4M3, synth.CI8, synth.CI4])
+@pytest.mark.parametrize("mode", [synth.C32, synth.C16F, synth.C16BF, synth.C8E4M3, synth.CI8, synth.CI4])
 @pytest.mark.parametrize("layout", [0, 1])
 def test_incoherent(bf, mode, layout):
     scene = small_scene(n_ant=24, n_chan=3, n_samp=300, sigma=3.0)
@@ -321,6 +321,14 @@ def test_incoherent(bf, mode, layout):
     P = plan.execute_incoherent(dev(xin)).cpu().numpy()
     plan.close()
     ref = oracle.incoherent(X64[:, :, mask == 1], 16)
+    mx, l2 = rel_errors(P, ref)
+    record("incoherent", mx, l2, mode=synth.MODE_NAMES[mode])
+    assert mx < 1e-5
+    # without a mask (the 16-byte load path for 16-bit samples, channel-major)
+    plan = bf.Plan(scene.pos, scene.freqs, synth.beam_grid(2, 2), mode, 16, layout)
+    P = plan.execute_incoherent(dev(xin)).cpu().numpy()
+    plan.close()
+    ref = oracle.incoherent(X64, 16)
     mx, l2 = rel_errors(P, ref)
     record("incoherent", mx, l2, mode=synth.MODE_NAMES[mode])
     assert mx < 1e-5
@@ -338,6 +346,26 @@ def test_corner_turn_bit_exact(bf, mode):
     torch.cuda.synchronize()
     got = out.cpu().numpy().view(x.dtype).reshape(x.shape)
     ref = oracle.corner_turn(nct, perm)                # [c][t][n](,2)
+    assert np.array_equal(got, ref.reshape(x.shape))
+
+
+@pytest.mark.parametrize("n_ant,n_samp,mode,use_perm", [
+    (40, 200, synth.C16F, True),     # 16-byte loads and stores (T % 4 == 0): partial antenna and sample tiles
+    (64, 256, synth.C16BF, False),   # 16-byte path, full tiles
+    (36, 70, synth.C16F, True),      # 4-byte loads, 16-byte stores (any T)
+    (32, 15625 // 125, synth.C16F, False),
+    (4, 3, synth.C16BF, True),       # smallest aligned antenna count, T < a tile
+])
+def test_corner_turn_vectorised_paths(bf, n_ant, n_samp, mode, use_perm):
+    scene = small_scene(n_ant=n_ant, n_chan=3, n_samp=n_samp, grid=False, sigma=4.0)
+    x = synth.voltages(scene, mode)
+    nct = synth.to_nct(x, mode)
+    perm = np.random.default_rng(n_ant).permutation(n_ant) if use_perm else None
+    out = torch.empty(x.nbytes, dtype=torch.uint8, device="cuda")
+    bf.bf_corner_turn(dev(nct).data_ptr(), mode, out.data_ptr(), mode, n_ant, 3, n_samp, perm=perm)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(x.dtype).reshape(x.shape)
+    ref = oracle.corner_turn(nct, perm)
     assert np.array_equal(got, ref.reshape(x.shape))
 
 
