@@ -105,8 +105,21 @@ struct UnitWalk {
     }
 };
 
+// What the epilogue and the store warp need to know about one tile, written
+// by the producer (which walks the units anyway) into a ring in shared
+// memory, so the 16 epilogue warps carry no walker state (their registers go
+// to the accumulator read-out).
+struct __align__(16) TileDesc {
+    const float *wscale;   // per-beam power scale rows of the job's first channel, or NULL
+    float *out;            // the job's powers, offset to its first channel
+    const float *acc_in;   // carried-window sums, offset likewise, or NULL
+    float *acc_out;
+    int b0, n_beams, b_pad, c, tt, T_o, c_total, last;   // last != 0: no more tiles
+};
+constexpr int kDescRing = 16;
+
 template <bool F8, int WIN>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, const __grid_constant__ ParamJobs pj)
+__global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_constant__ ParamJobs pj)
 {
     const BatchJob *jobs = a.jobs ? a.jobs : pj.j;   // a table in device memory, or jobs passed by value
     extern __shared__ uint8_t smem_raw[];
@@ -115,7 +128,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t sx = base;
     float *stage = reinterpret_cast<float *>(gbase + a.xst * a.stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
+    TileDesc *desc = reinterpret_cast<TileDesc *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(desc + kDescRing);
     const uint32_t b_full = smem_u32(bars + 0);                  // [kMaxXStages]
     const uint32_t b_empty = smem_u32(bars + kMaxXStages);       // [kMaxXStages]
     const uint32_t b_tfull = smem_u32(bars + 2 * kMaxXStages);   // [kMaxAcc]
@@ -123,7 +137,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
     const uint32_t b_drain = b_tempty + 8 * kMaxAcc;
     const uint32_t b_sfull = b_drain + 8;                         // [kStageDepth]
     const uint32_t b_sempty = b_sfull + 8 * kStageDepth;          // [kStageDepth]
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth);
+    const uint32_t b_dfull = b_sempty + 8 * kStageDepth;          // [kDescRing]
+    const uint32_t b_dempty = b_dfull + 8 * kDescRing;            // [kDescRing]
+    uint32_t *tmem_holder =
+        reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth + 2 * kDescRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -136,12 +153,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
         }
         for (int i = 0; i < a.nacc; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
-            mbar_init(b_tempty + 8 * i, kEpiWarps);
+            mbar_init(b_tempty + 8 * i, kEpiWarps / 2);   // one group releases each use
         }
         mbar_init(b_drain, 1);
         for (int i = 0; i < kStageDepth; ++i) {
             mbar_init(b_sfull + 8 * i, 4 * a.nsplit);
             mbar_init(b_sempty + 8 * i, 1);
+        }
+        for (int i = 0; i < kDescRing; ++i) {
+            mbar_init(b_dfull + 8 * i, 1);
+            mbar_init(b_dempty + 8 * i, 1);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -155,7 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t cnt = 0, issued = 0;
+            uint32_t cnt = 0, issued = 0, kt = 0;
             int st = 0;
             UnitWalk w;
             w.begin(jobs);
@@ -163,7 +184,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
             bool ok = true;
             const CUtensorMap *xmap = nullptr, *wmap = nullptr;
             int kbn = 0, ke = 0, t_shift = 0, c_base = 0;
+            TileDesc d{};
             const uint32_t bytes = 16384 + a.nt * 128;
+            // publishes one tile descriptor (after the store warp has released the slot)
+            auto publish = [&](const TileDesc &v) -> bool {
+                const uint32_t slot = kt % kDescRing;
+                if (!mbar_wait(b_dempty + 8 * slot, ((kt / kDescRing) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles))
+                    return false;
+                desc[slot] = v;
+                mbar_arrive(b_dfull + 8 * slot);
+                ++kt;
+                return true;
+            };
             while (ok && w.next(a, p)) {
                 if (w.fresh) {
                     const BatchJob &J = jobs[p.j];
@@ -175,7 +207,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
                     ke = J.ke;
                     t_shift = J.t_shift;
                     c_base = J.c_base;
+                    d.wscale = J.wscale ? J.wscale + (size_t)J.c_base * J.b_pad : nullptr;
+                    d.out = J.out + (size_t)J.c_base * J.T_o;
+                    d.acc_in = J.acc_in ? J.acc_in + J.c_base : nullptr;
+                    d.acc_out = J.acc_out ? J.acc_out + J.c_base : nullptr;
+                    d.n_beams = J.B;
+                    d.b_pad = J.b_pad;
+                    d.T_o = J.T_o;
+                    d.c_total = J.c_total;
                 }
+                d.b0 = p.m * kBeamsPerMTile;
+                d.c = p.c;
+                d.tt = p.tt;
+                d.last = 0;
+                if (!publish(d)) break;
                 for (int kb = 0; kb < kbn; ++kb) {
                     if (!mbar_wait(b_empty + 8 * st, ((cnt >> st) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
@@ -192,6 +237,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
                     if (++st == a.xst) st = 0;
                 }
             }
+            // two end markers: one for each epilogue group's next tile
+            d.last = 1;
+            if (!*abort_flag && publish(d)) publish(d);
             if (*abort_flag)
                 for (int i = 0; i < a.xst; ++i)
                     if (issued & (1u << i)) drain_wait(b_full + 8 * i, ((cnt >> i) & 1u) ^ 1u);
@@ -221,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
                 }
                 tpar ^= 1u << acc;
                 tc_fence_after();
-                const uint32_t d = tmem + acc * a.nt;
+                const uint32_t dacc = tmem + acc * a.nt;
                 for (int kb = 0; kb < kbn; ++kb) {
                     if (!mbar_wait(b_full + 8 * st, (par >> st) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                         ok = false;
@@ -238,8 +286,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
                         if (ks >= ksn) break;
                         const uint64_t ad = sdesc_sw128(sw + ks * 32);
                         const uint64_t bd = sdesc_sw128(sw + 16384 + ks * 32);
-                        if (F8) mma_f8(d, ad, bd, idesc, (kb | ks) != 0);
-                        else mma_f16(d, ad, bd, idesc, (kb | ks) != 0);
+                        if (F8) mma_f8(dacc, ad, bd, idesc, (kb | ks) != 0);
+                        else mma_f16(dacc, ad, bd, idesc, (kb | ks) != 0);
                     }
                     mma_commit(b_empty + 8 * st);
                     if (++st == a.xst) st = 0;
@@ -254,76 +302,60 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const BatchArgs a, c
         __syncwarp();
     } else if (warp < kStoreWarp) {
         // -------------------------------------------------------------- epilogue
+        // two groups of 8 warps take alternate tiles (and so alternate
+        // accumulators: nacc is even); in a group, two warps per TMEM lane
+        // quarter, each on a half of the tile's columns
         const int e = warp - 2;
+        const int grp = e >> 3;
         const int q = warp & 3;
-        const int h = e >> 2;
+        const int h = (e & 7) >> 2;
         const int bq = q * 16 + (lane & 15);
         const int cols = a.nt / a.nsplit;
         const int col0 = h * cols;
         const bool active = h < a.nsplit;
-        uint32_t tpar = 0, kt = 0;
-        int acc = 0;
-        UnitWalk w;
-        w.begin(jobs);
-        UnitPos p;
-        // the epilogue's view of the current job: only what the power epilogue
-        // reads, so few registers stay live across the tile loop
-        struct EpiView {
-            int t_int, b_pad;
-            const float *wscale;
-        } o{a.t_int, 0, nullptr};
-        int n_beams = 0;
-        while (w.next(a, p)) {
-            if (w.fresh) {   // per-channel scales offset to the job's first channel
-                const BatchJob &J = jobs[p.j];
-                n_beams = J.B;
-                o.b_pad = J.b_pad;
-                o.wscale = J.wscale ? J.wscale + (size_t)J.c_base * J.b_pad : nullptr;
-            }
-            if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
-            tpar ^= 1u << acc;
+        for (uint32_t kt = grp;; kt += 2) {
+            const uint32_t slot = kt % kDescRing;
+            if (!mbar_wait(b_dfull + 8 * slot, (kt / kDescRing) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+            const TileDesc &D = desc[slot];
+            if (D.last) break;
+            const int acc = (int)(kt % (uint32_t)a.nacc);
+            if (!mbar_wait(b_tfull + 8 * acc, (kt / a.nacc) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
             const uint32_t sb = kt % kStageDepth;
             if (active && !mbar_wait(b_sempty + 8 * sb, ((kt / kStageDepth) & 1u) ^ 1u, abort_flag, a.err,
                                      kWaitLimitCycles))
                 break;
             tc_fence_after();
-            const int b = p.m * kBeamsPerMTile + bq;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * a.nt + col0;
             const uint32_t tempty = b_tempty + 8 * acc;
             if (!active) {
                 tile_release(tempty, lane);
             } else {
-                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < n_beams, p.c,
+                struct {
+                    int t_int, b_pad;
+                    const float *wscale;
+                } o{a.t_int, D.b_pad, D.wscale};
+                const int b = D.b0 + bq;
+                epi_power_tile<WIN>(o, taddr, cols, h, lane, bq, b, b < D.n_beams, D.c,
                                     stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
             }
-            ++kt;
-            if (++acc == a.nacc) acc = 0;
         }
     } else if (warp == kStoreWarp) {
         // ------------------------------------------------------------ store warp
-        uint32_t kt = 0;
-        UnitWalk w;
-        w.begin(jobs);
-        UnitPos p;
-        TileOut o{a.nt, a.nsplit, a.wpt, a.t_int, 0, 0, 0, 0, 0, nullptr, nullptr, nullptr};
-        while (w.next(a, p)) {
-            if (w.fresh) {   // outputs offset to the job's first channel
-                const BatchJob &J = jobs[p.j];
-                o.T = J.T;
-                o.T_o = J.T_o;
-                o.B = J.B;
-                o.b_pad = J.b_pad;
-                o.c_total = J.c_total;
-                o.out = J.out + (size_t)J.c_base * J.T_o;
-                o.acc_in = J.acc_in ? J.acc_in + J.c_base : nullptr;
-                o.acc_out = J.acc_out ? J.acc_out + J.c_base : nullptr;
-            }
+        for (uint32_t kt = 0;; ++kt) {
+            const uint32_t slot = kt % kDescRing;
+            if (!mbar_wait(b_dfull + 8 * slot, (kt / kDescRing) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+            const TileDesc &D = desc[slot];
+            if (D.last) break;
             const uint32_t sb = kt % kStageDepth;
             if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
-            store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), p.m * kBeamsPerMTile, p.c, p.tt, lane);
+            const TileOut o{a.nt,    a.nsplit, a.wpt, a.t_int, 0, D.T_o, D.n_beams, D.b_pad, D.c_total,
+                            D.wscale, nullptr,  D.out, D.acc_in, D.acc_out};
+            store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), D.b0, D.c, D.tt, lane);
             __syncwarp();
-            if (lane == 0) mbar_arrive_relaxed(b_sempty + 8 * sb);
-            ++kt;
+            if (lane == 0) {
+                mbar_arrive_relaxed(b_sempty + 8 * sb);
+                mbar_arrive(b_dempty + 8 * slot);   // the producer may reuse the descriptor slot
+            }
         }
     }
 
@@ -344,7 +376,8 @@ static int batch_stage_bytes(int nt) { return 16384 + nt * 128; }
 static int batch_layout_end(int xst, int nt)
 {
     return 1024 + xst * batch_stage_bytes(nt) + kStageDepth * kBeamsPerMTile * kMaxWinPerTile * 4 +
-           8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth) + 8;
+           kDescRing * (int)sizeof(TileDesc) + 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth + 2 * kDescRing) +
+           8;
 }
 
 // The attribute is a per-kernel maximum shared by every batch: it is set to
@@ -428,7 +461,7 @@ bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int til
     c.t_int = t_int;
     c.nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
     c.wpt = nt / t_int;
-    c.nacc = std::min(kMaxAcc, kTmemCols / nt);
+    c.nacc = std::min(kMaxAcc, kTmemCols / nt) & ~1;   // even: each epilogue group keeps its own accumulators
     c.f8 = p0->wf.op == kOpE4M3;
     c.num_sms = std::max(1, p0->num_sms);
     const int fixed = batch_layout_end(0, nt);

@@ -13,7 +13,7 @@
 
 namespace bfi {
 
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;                      // two groups of 8 taking alternate tiles
 constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
 constexpr int kTcThreads = (3 + kEpiWarps) * 32;
 constexpr int kStageDepth = 4;                     // staged tiles in flight
