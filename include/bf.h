@@ -216,6 +216,19 @@ bf_status bf_plan_query_tiles(const bf_plan *plan, int *tile_t, int *group_tiles
 bf_status bf_plan_set_input_order(bf_plan *plan, const int *perm);
 
 /*
+ * bf_plan_set_weight_buffers — n = 2: the plan keeps two weight buffers, and
+ * bf_weights (tracking: re-pointing every chunk, Section 3) regenerates into
+ * the one not in use on a plan-owned stream, after the last execute that
+ * read it, then makes it current; executes on any stream wait for the latest
+ * refresh (stream-ordered, no host synchronisation).  So the refresh for the
+ * next chunk overlaps the beamforming of the current one.  Costs one more
+ * copy of the weights in device memory.  n = 1 (the default) frees it.
+ * Synchronises the plan's streams.  A plan with two buffers cannot join a
+ * batch or a server.  Errors: BF_ERR_ARG, BF_ERR_NOMEM.
+ */
+bf_status bf_plan_set_weight_buffers(bf_plan *plan, int n);
+
+/*
  * bf_plan_query — report the plan's choices (any output pointer may be NULL):
  *  kernel (bf_kernel actually used), tile_t, beams per weight group resident
  *  in shared memory (tensor-core kernel), and bytes of device memory owned.

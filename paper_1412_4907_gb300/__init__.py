@@ -58,6 +58,7 @@ SIGNATURES = {
     "bf_plan_set_kernel": [_P, _I, _I],
     "bf_plan_set_input_order": [_P, _P],
     "bf_plan_set_tiles": [_P, _I, _I, _I],
+    "bf_plan_set_weight_buffers": [_P, _I],
     "bf_plan_query_tiles": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "bf_plan_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_S)],
     "bf_export_weights": [_P, _P, _P],
@@ -178,6 +179,10 @@ def bf_plan_query_tiles(plan: int) -> dict:
     t, g, x, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(_lib.bf_plan_query_tiles(plan, ctypes.byref(t), ctypes.byref(g), ctypes.byref(x), ctypes.byref(n)))
     return {"tile_t": t.value, "group_tiles": g.value, "x_stages": x.value, "n_groups": n.value}
+
+
+def bf_plan_set_weight_buffers(plan: int, n: int):
+    _check(_lib.bf_plan_set_weight_buffers(plan, n))
 
 
 def bf_plan_set_input_order(plan: int, perm=None):
@@ -390,6 +395,9 @@ class Plan:
 
     def query_tiles(self) -> dict:
         return bf_plan_query_tiles(self.handle)
+
+    def set_weight_buffers(self, n: int):
+        bf_plan_set_weight_buffers(self.handle, n)
 
     def set_input_order(self, perm):
         bf_plan_set_input_order(self.handle, perm)

@@ -57,6 +57,16 @@ static void plan_free(bf_plan *p)
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->stream2) cudaStreamSynchronize(p->stream2);
     if (p->stream3) cudaStreamSynchronize(p->stream3);
+    if (p->wstream) cudaStreamSynchronize(p->wstream);
+    if (p->wbufs == 2) {   // the buffers that are not the current ones
+        const int o = 1 - p->wcur;
+        if (p->wbuf[o]) cudaFree(p->wbuf[o]);
+        if (p->wscale_buf[o]) cudaFree(p->wscale_buf[o]);
+        if (p->wsig_buf[o]) cudaFree(p->wsig_buf[o]);
+    }
+    for (cudaEvent_t ev : {p->ev_wready, p->ev_wused[0], p->ev_wused[1]})
+        if (ev) cudaEventDestroy(ev);
+    if (p->wstream) cudaStreamDestroy(p->wstream);
     void *ptrs[] = {p->d_pos, p->d_freqs, p->d_dirs, p->d_mask, p->d_tau, p->d_ab, p->d_w, p->d_wscale,
                     p->d_wsig, p->d_scratch, p->d_hx, p->d_hp, p->d_err};
     for (void *q : ptrs)
@@ -88,8 +98,35 @@ static bf_status upload_geometry(bf_plan *p)
 
 static bf_status regenerate(bf_plan *p)
 {
+    if (p->wbufs == 2) {
+        // fill the other buffer on the weight stream once the last execute that
+        // read it is done, then make it current; executes wait for ev_wready
+        const int back = 1 - p->wcur;
+        BF_CUDA(cudaStreamWaitEvent(p->wstream, p->ev_wused[back], 0), "weight stream ordering");
+        p->wcur = back;
+        p->d_w = p->wbuf[back];
+        p->d_wscale = p->wscale_buf[back];
+        p->d_wsig = p->wsig_buf[back];
+        BF_CUDA(launch_delays(p, p->wstream), "delay kernel");
+        BF_CUDA(launch_weights(p, p->wstream), "weight kernel");
+        BF_CUDA(cudaEventRecord(p->ev_wready, p->wstream), "weight event");
+        return BF_OK;
+    }
     BF_CUDA(launch_delays(p, p->stream), "delay kernel");
     BF_CUDA(launch_weights(p, p->stream), "weight kernel");
+    return BF_OK;
+}
+
+// Stream-order an execute on s after the latest weight refresh, and (after
+// its launches) mark the current buffer as read by s.
+static bf_status weights_acquire(bf_plan *p, cudaStream_t s)
+{
+    if (p->wbufs == 2) BF_CUDA(cudaStreamWaitEvent(s, p->ev_wready, 0), "weight ordering");
+    return BF_OK;
+}
+static bf_status weights_release(bf_plan *p, cudaStream_t s)
+{
+    if (p->wbufs == 2) BF_CUDA(cudaEventRecord(p->ev_wused[p->wcur], s), "weight event");
     return BF_OK;
 }
 
@@ -238,7 +275,7 @@ bf_status bf_weights(bf_plan *p, const double *dirs)
         if (st != BF_OK) return st;
         p->dirs.assign(dirs, dirs + 3 * (size_t)p->B);
         BF_CUDA(cudaMemcpyAsync(p->d_dirs, p->dirs.data(), 3 * (size_t)p->B * sizeof(double),
-                                cudaMemcpyHostToDevice, p->stream),
+                                cudaMemcpyHostToDevice, p->wbufs == 2 ? p->wstream : p->stream),
                 "copy directions");
     }
     return regenerate(p);
@@ -284,8 +321,8 @@ static bf_status ensure(void **ptr, size_t *have, size_t need, bf_plan *p, const
 
 // Run the beamformer on channels [c_base, c_base + c_launch) whose voltages
 // start at x (CTN) or on all channels (NCT, c_base = 0).
-static bf_status run_range(bf_plan *p, const void *x, int c_base, int c_launch, int T, float *out, int mode,
-                           cudaStream_t s)
+static bf_status run_range_body(bf_plan *p, const void *x, int c_base, int c_launch, int T, float *out, int mode,
+                                cudaStream_t s)
 {
     const int T_o = T / p->t_int;
     if (mode == 2) {   // incoherent
@@ -356,6 +393,17 @@ static bf_status run_range(bf_plan *p, const void *x, int c_base, int c_launch, 
         return cuda_error(e, "tensor-core kernel");
     }
     return BF_OK;
+}
+
+// One launch range with the weight ordering of double-buffered plans.
+static bf_status run_range(bf_plan *p, const void *x, int c_base, int c_launch, int T, float *out, int mode,
+                           cudaStream_t s)
+{
+    if (mode == 2) return run_range_body(p, x, c_base, c_launch, T, out, mode, s);   // no weights
+    bf_status st = weights_acquire(p, s);
+    if (st == BF_OK) st = run_range_body(p, x, c_base, c_launch, T, out, mode, s);
+    if (st == BF_OK) st = weights_release(p, s);
+    return st;
 }
 
 // Returns BF_OK with *noop set when the call has nothing to compute.
@@ -452,6 +500,7 @@ bf_status bf_sync(bf_plan *p)
     BF_CUDA(cudaStreamSynchronize(p->stream), "stream synchronize");
     BF_CUDA(cudaStreamSynchronize(p->stream2), "stream synchronize");
     BF_CUDA(cudaStreamSynchronize(p->stream3), "stream synchronize");
+    if (p->wstream) BF_CUDA(cudaStreamSynchronize(p->wstream), "stream synchronize");
     unsigned err = 0;
     BF_CUDA(cudaMemcpy(&err, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status word");
     if (err) {
@@ -501,6 +550,53 @@ bf_status bf_plan_set_tiles(bf_plan *p, int tile_t, int group_tiles, int x_stage
     return BF_OK;
 }
 
+bf_status bf_plan_set_weight_buffers(bf_plan *p, int n)
+{
+    g_last_error.clear();
+    if (!p) return set_error(BF_ERR_ARG, "plan is NULL");
+    if (n != 1 && n != 2) return set_error(BF_ERR_ARG, "weight buffers must be 1 or 2");
+    if (n == p->wbufs) return BF_OK;
+    BF_CUDA(cudaStreamSynchronize(p->stream), "stream synchronize");
+    if (p->wstream) BF_CUDA(cudaStreamSynchronize(p->wstream), "stream synchronize");
+    const size_t sb = (size_t)p->C * p->wf.b_pad * sizeof(float);
+    if (n == 2) {
+        void *w = nullptr;
+        float *sc = nullptr, *sg = nullptr;
+        cudaError_t e = cudaMalloc(&w, p->w_bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sc, sb);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sg, sb);
+        if (e == cudaSuccess && !p->wstream) e = cudaStreamCreateWithFlags(&p->wstream, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&p->ev_wready, &p->ev_wused[0], &p->ev_wused[1]})
+            if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (w) cudaFree(w);
+            if (sc) cudaFree(sc);
+            if (sg) cudaFree(sg);
+            return cuda_error(e, "second weight buffer");
+        }
+        p->wbuf[0] = p->d_w;
+        p->wscale_buf[0] = p->d_wscale;
+        p->wsig_buf[0] = p->d_wsig;
+        p->wbuf[1] = w;
+        p->wscale_buf[1] = sc;
+        p->wsig_buf[1] = sg;
+        p->wcur = 0;
+        p->wbufs = 2;
+        p->dev_bytes += p->w_bytes + 2 * sb;
+        return BF_OK;
+    }
+    const int o = 1 - p->wcur;   // keep the current buffer
+    cudaFree(p->wbuf[o]);
+    cudaFree(p->wscale_buf[o]);
+    cudaFree(p->wsig_buf[o]);
+    p->wbuf[0] = p->wbuf[1] = nullptr;
+    p->wscale_buf[0] = p->wscale_buf[1] = p->wsig_buf[0] = p->wsig_buf[1] = nullptr;
+    p->wcur = 0;
+    p->wbufs = 1;
+    p->dev_bytes -= p->w_bytes + 2 * sb;
+    return BF_OK;
+}
+
 bf_status bf_plan_query(const bf_plan *p, int *kernel, int *tile_t, int *group_tiles, size_t *device_bytes)
 {
     g_last_error.clear();
@@ -528,8 +624,10 @@ bf_status bf_export_weights(bf_plan *p, float *d_w, float *d_scale)
 {
     g_last_error.clear();
     if (!p || !d_w) return set_error(BF_ERR_ARG, "NULL plan or output");
+    bf_status st = weights_acquire(p, p->stream);
+    if (st != BF_OK) return st;
     BF_CUDA(launch_export_weights(p, d_w, d_scale, p->stream), "weight export");
-    return BF_OK;
+    return weights_release(p, p->stream);
 }
 
 bf_status bf_corner_turn(const void *d_in, int in_dtype, void *d_out, int out_dtype, int n_ant, int n_chan,

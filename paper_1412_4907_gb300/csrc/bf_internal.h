@@ -107,6 +107,15 @@ struct bf_plan {
     float *d_hp = nullptr;            // bf_execute_host staging (powers)
     size_t hp_bytes = 0;
 
+    // double-buffered weights (bf_plan_set_weight_buffers): the refresh fills
+    // the other buffer on wstream while executes read the current one
+    int wbufs = 1, wcur = 0;
+    void *wbuf[2] = {nullptr, nullptr};
+    float *wscale_buf[2] = {nullptr, nullptr}, *wsig_buf[2] = {nullptr, nullptr};
+    cudaStream_t wstream = nullptr;
+    cudaEvent_t ev_wready = nullptr;                  // the latest refresh is complete
+    cudaEvent_t ev_wused[2] = {nullptr, nullptr};     // the last execute that read buffer i
+
     unsigned *d_err = nullptr;        // device-side status word
     size_t dev_bytes = 0;
 };

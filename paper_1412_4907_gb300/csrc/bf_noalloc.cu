@@ -66,6 +66,10 @@ extern "C" bf_status bf_execute_nct_static(bf_plan *p, const void *x, int T, flo
     void *scr = nullptr;
     if ((e = static_scratch(dev, &scr)) != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
     cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
+    if (p->wbufs == 2) {   // stream-ordered after the latest weight refresh
+        e = cudaStreamWaitEvent(s, p->ev_wready, 0);
+        if (e != cudaSuccess) return cuda_error(e, "weight ordering");
+    }
     uint8_t *base = (uint8_t *)scr;
     e = launch_corner_turn(x, p->dtype, base, p->dtype, p->N, p->C, T, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "corner turn");
@@ -91,5 +95,7 @@ extern "C" bf_status bf_execute_nct_static(bf_plan *p, const void *x, int T, flo
         if (!why.empty()) return set_error(BF_ERR_CUDA, "tensor-core kernel: " + why);
         return cuda_error(e, "tensor-core kernel");
     }
+    if (p->wbufs == 2 && (e = cudaEventRecord(p->ev_wused[p->wcur], s)) != cudaSuccess)
+        return cuda_error(e, "weight event");
     return BF_OK;
 }

@@ -632,6 +632,9 @@ bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, in
 {
     if (!out) return set_error(BF_ERR_ARG, "out is NULL");
     *out = nullptr;
+    for (int i = 0; plans && i < n_plans; ++i)   // the batch keeps the plans' weight pointers
+        if (plans[i] && plans[i]->wbufs != 1)
+            return set_error(BF_ERR_UNSUPPORTED, "plans with double-buffered weights cannot join a batch");
     BatchCore core;
     bf_status st = batch_core_init(&core, plans, n_plans, tile_t);
     if (st != BF_OK) return st;

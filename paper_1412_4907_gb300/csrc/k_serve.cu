@@ -518,6 +518,9 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
     if (mem_bytes < 4096) return set_error(BF_ERR_ARG, "memory budget too small");
     if (n_configs > kParamJobs)
         return set_error(BF_ERR_UNSUPPORTED, "a server takes at most " + std::to_string(kParamJobs) + " streams");
+    for (int i = 0; plans && i < n_configs; ++i)
+        if (plans[i] && plans[i]->wbufs != 1)
+            return set_error(BF_ERR_UNSUPPORTED, "plans with double-buffered weights cannot join a server");
     BatchCore core;
     bf_status st = batch_core_init(&core, plans, n_configs, tile_t);
     if (st != BF_OK) return st;

@@ -605,16 +605,19 @@ static bool weights2_launch(bf_plan *p, cudaStream_t s)
     g.m_pad = f.m_pad;
     if (g.n_cols > 512) return false;
     g.tpb = g.n_cols <= 32 ? 32 : g.n_cols <= 64 ? 64 : g.n_cols <= 128 ? 128 : 256;
-    g.bpb = 256 / g.tpb;
+    // 128-thread blocks where a beam fits (5K registers a block), so a refresh
+    // on a side stream can share SMs with a running beamformer launch
+    const int wt = g.tpb <= 128 ? 128 : 256;
+    g.bpb = wt / g.tpb;
     g.apt = (g.n_cols + g.tpb - 1) / g.tpb;
     const int beam_blocks = (g.b_pad + g.bpb - 1) / g.bpb;
     // enough blocks to fill the GPU a few times over, each running many channels
-    const int target = 8 * p->num_sms * (2048 / 256);
+    const int target = 8 * p->num_sms * (2048 / wt);
     int chunks = std::max(1, std::min(p->C, (target + beam_blocks - 1) / beam_blocks));
     g.cc = (p->C + chunks - 1) / chunks;
     chunks = (p->C + g.cc - 1) / g.cc;
     dim3 grid(beam_blocks, chunks);
-#define BF_W2(F) k_weights2<F, FIXED><<<grid, 256, 0, s>>>(p->d_freqs, p->d_tau, p->d_ab, p->d_mask, g, p->C, \
+#define BF_W2(F) k_weights2<F, FIXED><<<grid, wt, 0, s>>>(p->d_freqs, p->d_tau, p->d_ab, p->d_mask, g, p->C, \
                                                            p->d_w, p->d_wscale, p->d_wsig)
     switch (fmt_code(p)) {
     case kFmtF16: BF_W2(kFmtF16); break;

@@ -88,6 +88,7 @@ def test_null_and_bad_handles(bf):
     assert lib.bf_batch_sync(None) == bf.BF_ERR_ARG
     assert lib.bf_batch_query(None, None, None, None) == bf.BF_ERR_ARG
     assert lib.bf_batch_destroy(None) == bf.BF_OK
+    assert lib.bf_plan_set_weight_buffers(None, 2) == bf.BF_ERR_ARG
     assert lib.bf_server_create(ctypes.byref(b), None, 1, 1 << 20, 2, 0) == bf.BF_ERR_ARG
     assert lib.bf_server_create(ctypes.byref(b), None, 1, 1 << 20, 0, 0) == bf.BF_ERR_ARG
     assert lib.bf_server_submit(None, 0, None, 1, None, None) == bf.BF_ERR_ARG

@@ -429,6 +429,42 @@ def test_tracking_update_equals_fresh_plan(bf):
     assert np.array_equal(P1, P2)
 
 
+@pytest.mark.parametrize("n_ant,mode", [(32, synth.C16F), (256, synth.C16F), (64, synth.CI8)])
+def test_double_buffered_tracking(bf, n_ant, mode):
+    """Two weight buffers: every chunk re-points the beams (the refresh runs on
+    the plan's weight stream while the previous chunk is beamformed on
+    another stream); each chunk's powers must be those of its own pointing,
+    bit-identical to a single-buffered plan given the same sequence."""
+    sigma = 16.0 if mode == synth.CI8 else 0.7071
+    scene = small_scene(n_ant=n_ant, n_chan=2, n_samp=512, grid=n_ant == 32, sigma=sigma)
+    x, _ = stored_voltages(scene, mode)
+    xd = dev(x)
+    pointings = [synth.beam_grid(8, 8, w) for w in (10.0, 4.0, 7.0, 2.0, 9.0, 5.0)]
+    other = torch.cuda.Stream()
+    single = bf.Plan(scene.pos, scene.freqs, pointings[0], mode, 64)
+    want = []
+    for d in pointings:
+        single.weights(d)
+        want.append(single.execute(xd).clone())
+    single.sync()
+    single.close()
+    plan = bf.Plan(scene.pos, scene.freqs, pointings[0], mode, 64, stream=other)
+    plan.set_weight_buffers(2)
+    got = []
+    with torch.cuda.stream(other):
+        for d in pointings:
+            plan.weights(d)           # enqueued on the weight stream, no host wait
+            got.append(plan.execute(xd))
+    plan.sync()
+    for i, (g, w) in enumerate(zip(got, want)):
+        assert torch.equal(g, w), i
+    plan.set_weight_buffers(1)
+    plan.weights(pointings[2])
+    assert torch.equal(plan.execute(xd), want[2])
+    plan.sync()
+    plan.close()
+
+
 def test_empty_and_short_inputs(bf):
     scene = small_scene(n_ant=32, n_chan=2, n_samp=40)
     dirs = synth.beam_grid(4, 4)
