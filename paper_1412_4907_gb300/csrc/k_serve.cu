@@ -109,7 +109,6 @@ struct Stream {   // one configuration: its plan and its open window
     float *acc[2] = {nullptr, nullptr};   // [B][C] partial window sums (ping-pong)
     int cur = 0;                          // acc[cur] holds the open window
     int carry = 0;                        // samples in the open window
-    long long queued = 0;                 // pending chunks of this stream
 };
 
 struct Slot {
@@ -234,7 +233,6 @@ static std::vector<Request *> admit(bf_server *s)
         ++ahead[r->cfg];
         got.push_back(r);
         it = s->pending.erase(it);
-        --st.queued;
     }
     return got;
 }
@@ -598,7 +596,6 @@ bf_status bf_server_submit(bf_server *s, int config, const void *h_voltages, int
         r->id = s->next_id++;
         r->t_submit = now_s();
         s->pending.push_back(r);
-        ++s->streams[config].queued;
         ++s->submitted;
     }
     s->cv.notify_all();

@@ -203,6 +203,12 @@ def test_batch_rejections(bf):
     with pytest.raises(bf.BFError) as ei:
         bf.Batch([p16], tile_t=72)   # not a multiple of 16 and T_int
     assert ei.value.status == bf.BF_ERR_UNSUPPORTED
+    pdb = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C16F, 64)
+    pdb.set_weight_buffers(2)        # the batch would hold a weight pointer that moves
+    with pytest.raises(bf.BFError) as ei:
+        bf.Batch([p16, pdb])
+    assert ei.value.status == bf.BF_ERR_UNSUPPORTED
+    pdb.close()
     batch = bf.Batch([p16, p16])
     with pytest.raises(bf.BFError) as ei:
         batch.execute()   # jobs not bound
