@@ -256,6 +256,11 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
             bool ok = true;
             int kbn = 0, ks_last = 4;
             uint32_t idesc = 0;
+            // descriptor words of stage 0; a stage's operands are an offset added to the
+            // low word (start address in 16-byte units; no carry below 256 KB)
+            const uint64_t s_desc0 = sdesc_sw128(sx);
+            const uint32_t s_hi = (uint32_t)(s_desc0 >> 32), s_lo0 = (uint32_t)s_desc0;
+            const uint32_t stage16 = a.stage_bytes >> 4;
             while (ok && w.next(a, p)) {
                 if (w.fresh) {
                     const BatchJob &J = jobs[p.j];
@@ -277,17 +282,15 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
                     }
                     par ^= 1u << st;
                     tc_fence_after();
-                    const uint32_t sw = sx + st * a.stage_bytes;
+                    const uint32_t wl = s_lo0 + st * stage16, xl = wl + (16384 >> 4);
                     // the last K block may hold fewer than 4 k-steps of antennas (the
                     // rest is zero padding): those MMAs are skipped
                     const int ksn = kb + 1 == kbn ? ks_last : 4;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         if (ks >= ksn) break;
-                        const uint64_t ad = sdesc_sw128(sw + ks * 32);
-                        const uint64_t bd = sdesc_sw128(sw + 16384 + ks * 32);
-                        if (F8) mma_f8(dacc, ad, bd, idesc, (kb | ks) != 0);
-                        else mma_f16(dacc, ad, bd, idesc, (kb | ks) != 0);
+                        if (F8) mma_f8_w(dacc, wl + 2 * ks, s_hi, xl + 2 * ks, s_hi, idesc, (kb | ks) != 0);
+                        else mma_f16_w(dacc, wl + 2 * ks, s_hi, xl + 2 * ks, s_hi, idesc, (kb | ks) != 0);
                     }
                     mma_commit(b_empty + 8 * st);
                     if (++st == a.xst) st = 0;

@@ -353,6 +353,16 @@ __global__ void __maxnreg__(96)
             uint32_t xpar = 0, wpar = 0, tpar = 0;
             int xs = 0, acc = 0;
             bool ok = true;
+            // Descriptor words of the first weight slot and the first voltage stage;
+            // every operand address below is an offset from these, added to the low
+            // word (shared memory is below 256 KB, so the 14-bit start-address field
+            // never carries).  Building each 64-bit descriptor anew made the issue of
+            // one tcgen05.mma cost ~75-90 cycles; with one add it is ~50.
+            const uint64_t w_desc0 = sdesc_sw128(sw), x_desc0 = sdesc_sw128(sx);
+            const uint32_t w_hi = (uint32_t)(w_desc0 >> 32), x_hi = (uint32_t)(x_desc0 >> 32);
+            const uint32_t w_lo0 = (uint32_t)w_desc0, x_lo0 = (uint32_t)x_desc0;
+            const uint32_t w_slot16 = a.w_slot_bytes >> 4, x_stage16 = a.x_stage_bytes >> 4;
+            const uint32_t x_kb16 = (uint32_t)(a.nt * 128) >> 4;
             for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
                 int m0, gs;
                 group_tiles(a, g, m0, gs);
@@ -382,13 +392,12 @@ __global__ void __maxnreg__(96)
                         tpar ^= 1u << acc;
                         tc_fence_after();
                         const uint32_t d = tmem + acc * a.nt;
-                        for (int kb = 0; kb < a.kb; ++kb)
+                        uint32_t wl = w_lo0 + s * w_slot16, xl = x_lo0 + xs * x_stage16;
+                        for (int kb = 0; kb < a.kb; ++kb, wl += 16384 >> 4, xl += x_kb16)
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {   // 32-byte K steps per 128-byte block
-                                const uint64_t ad = sdesc_sw128(sw + s * a.w_slot_bytes + kb * 16384 + ks * 32);
-                                const uint64_t bd = sdesc_sw128(sx + xs * a.x_stage_bytes + kb * a.nt * 128 + ks * 32);
-                                if (F8) mma_f8(d, ad, bd, a.idesc, (kb | ks) != 0);
-                                else mma_f16(d, ad, bd, a.idesc, (kb | ks) != 0);
+                                if (F8) mma_f8_w(d, wl + 2 * ks, w_hi, xl + 2 * ks, x_hi, a.idesc, (kb | ks) != 0);
+                                else mma_f16_w(d, wl + 2 * ks, w_hi, xl + 2 * ks, x_hi, a.idesc, (kb | ks) != 0);
                             }
                         mma_commit(b_tfull + 8 * acc);
                         if (lastw) mma_commit(b_wempty + 8 * s);
@@ -437,14 +446,6 @@ __global__ void __maxnreg__(96)
                     tpar ^= 1u << acc;
                     const uint32_t sb = kt % kStageDepth;
                     const uint32_t use = kt / kStageDepth;
-                    if (!COMPLEX && active) {
-                        // this staging buffer is free once the store warp has written out
-                        // the tile that used it kStageDepth tiles ago
-                        if (!mbar_wait(b_sempty + 8 * sb, (use & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
-                            ok = false;
-                            break;
-                        }
-                    }
                     tc_fence_after();
                     const int b = (m0 + s) * kBeamsPerMTile + bq;
                     const bool bvalid = b < a.B;
@@ -487,8 +488,18 @@ __global__ void __maxnreg__(96)
                         float *stg = stage + sb * (kBeamsPerMTile * kMaxWinPerTile);
                         float ws = 0.f;
                         int wi = 0, cnt = 0;
+                        bool staged = false;
                         auto emit = [&](float sum) {
                             const float pw = (sum + __shfl_xor_sync(0xffffffffu, sum, 16)) * scale;
+                            if (!staged) {
+                                // the staging buffer is free once the store warp has written out the
+                                // tile that used it kStageDepth tiles ago; waited for here, after the
+                                // accumulator (or its first slice) is read, so that this wait is not
+                                // in the path between the MMA and the read-out
+                                staged = true;
+                                if (!mbar_wait(b_sempty + 8 * sb, (use & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles))
+                                    ok = false;
+                            }
                             if (part == 0) stg[bq * kMaxWinPerTile + h * wps + wi] = pw;
                             ++wi;
                         };
@@ -542,6 +553,7 @@ __global__ void __maxnreg__(96)
                         if (lane == 0) mbar_arrive(b_sfull + 8 * sb);   // publishes the staged windows
                     }
                     if (++acc == a.nacc) acc = 0;
+                    if (!ok) break;
                 }
                 if (++tt == a.t_tiles) {
                     tt = 0;
@@ -555,6 +567,7 @@ __global__ void __maxnreg__(96)
         uint32_t kt = 0;
         bool ok = true;
         const bool vec = (a.T_o & 3) == 0 && (a.wpt & 3) == 0;
+        const bool vec2 = (a.T_o & 1) == 0 && (a.wpt & 1) == 0;
         for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
             int m0, gs;
             group_tiles(a, g, m0, gs);
@@ -580,6 +593,17 @@ __global__ void __maxnreg__(96)
                             if (bb < a.B && nj > 0) {
                                 const float4 v4 = *reinterpret_cast<const float4 *>(stg + bl * kMaxWinPerTile);
                                 *reinterpret_cast<float4 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o + j0) = v4;
+                            }
+                        }
+                    } else if (vec2 && a.wpt == 2) {
+                        // one float2 per beam
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int bl = lane + 32 * r;
+                            const int bb = b_tile0 + bl;
+                            if (bb < a.B && nj > 0) {
+                                const float2 v2 = *reinterpret_cast<const float2 *>(stg + bl * kMaxWinPerTile);
+                                *reinterpret_cast<float2 *>(a.out + ((size_t)bb * a.c_total + cg) * a.T_o + j0) = v2;
                             }
                         }
                     } else if (vec) {
