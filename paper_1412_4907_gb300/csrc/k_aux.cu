@@ -280,23 +280,35 @@ __global__ void k_incoherent(const void *__restrict__ x, const uint8_t *__restri
         }
     } else if ((DT == BF_C16F || DT == BF_C16BF) && !mask && (n_el & 3) == 0 && ((uintptr_t)x & 15) == 0 &&
                ((((size_t)c * T + (size_t)j * t_int) * N) & 3) == 0) {
-        // 16-bit samples, no mask, aligned window: 16-byte loads of 4 samples
+        // 16-bit samples, no mask, aligned window: 16-byte loads of 4 samples,
+        // eight loads in flight per lane (issued unconditionally before any is
+        // used: past the window's end they re-read its last 16 bytes and are
+        // replaced by zeros), summed in the same per-lane order as one load at
+        // a time
         const uint4 *w4 = reinterpret_cast<const uint4 *>(x) + (((size_t)c * T + (size_t)j * t_int) * N >> 2);
         const int n4 = n_el >> 2;
-#pragma unroll 4
-        for (int i = lane; i < n4; i += 32) {
-            const uint4 q = w4[i];
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+        constexpr int kDepth = 8;
+        for (int i0 = lane; i0 < n4; i0 += 32 * kDepth) {
+            uint4 q[kDepth];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float2 v;
-                if constexpr (DT == BF_C16F) {
-                    v = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
-                } else {
-                    v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[k]));
+            for (int k = 0; k < kDepth; ++k) q[k] = __ldcs(w4 + min(i0 + 32 * k, n4 - 1));   // unconditional
+#pragma unroll
+            for (int k = 0; k < kDepth; ++k)
+                if (i0 + 32 * k >= n4) q[k] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int k = 0; k < kDepth; ++k) {
+                const uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float2 v;
+                    if constexpr (DT == BF_C16F) {
+                        v = __half22float2(*reinterpret_cast<const __half2 *>(&w[e]));
+                    } else {
+                        v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[e]));
+                    }
+                    s0 = fmaf(v.x, v.x, s0);
+                    s1 = fmaf(v.y, v.y, s1);
                 }
-                s0 = fmaf(v.x, v.x, s0);
-                s1 = fmaf(v.y, v.y, s1);
             }
         }
     } else {

@@ -5,8 +5,8 @@
 // follow the beamformer in the transient pipeline of Section 3 (Table 3);
 // the paper names the stages without formulas.
 //
-// One warp per (beam, channel) row, three passes over the row (it stays in
-// L1 after the first), all in FP32 with a fixed reduction order (lane-strided
+// One warp per (beam, channel) row, three passes over the row (in registers
+// for rows of up to 256 windows, else re-read from L1), all in FP32 with a fixed reduction order (lane-strided
 // partial sums, then a butterfly), so the result does not depend on the
 // launch shape: the mean, then the population variance as the mean of the
 // squared deviations from it (two passes: no cancellation), then z =
@@ -24,6 +24,8 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+constexpr int kRowRegs = 8;   // rows of up to 256 windows are held in registers
+
 __global__ void k_detect(const float *__restrict__ P, int rows, int n_win, float k_sigma, float *__restrict__ z_out,
                          int *__restrict__ hits, int max_hits, int *__restrict__ n_hits, int n_chan)
 {
@@ -31,6 +33,49 @@ __global__ void k_detect(const float *__restrict__ P, int rows, int n_win, float
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= rows) return;
     const float *p = P + row * n_win;
+    const int b = (int)(row / n_chan), c = (int)(row % n_chan);
+    auto hit = [&](float z, int j) {
+        if (z > k_sigma) {
+            const int k = atomicAdd(n_hits, 1);
+            if (k < max_hits) {
+                hits[3 * k] = b;
+                hits[3 * k + 1] = c;
+                hits[3 * k + 2] = j;
+            }
+        }
+    };
+    if (n_win <= 32 * kRowRegs) {
+        // the row in registers: every load issued before any is used (indices
+        // clamped to the row, the surplus masked), then the three passes run
+        // on registers in the same per-lane order as the loops below
+        float r[kRowRegs];
+#pragma unroll
+        for (int k = 0; k < kRowRegs; ++k) r[k] = __ldcs(p + min(lane + 32 * k, n_win - 1));
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < kRowRegs; ++k)
+            if (lane + 32 * k < n_win) s += r[k];
+        const float mu_f = warp_sum(s) / (float)n_win;
+        float v = 0.f;
+#pragma unroll
+        for (int k = 0; k < kRowRegs; ++k)
+            if (lane + 32 * k < n_win) {
+                const float d = r[k] - mu_f;
+                v = fmaf(d, d, v);
+            }
+        const float var = warp_sum(v) / (float)n_win;
+        const float inv = var > 0.f ? 1.f / sqrtf(var) : 0.f;
+#pragma unroll
+        for (int k = 0; k < kRowRegs; ++k) {
+            const int j = lane + 32 * k;
+            if (j < n_win) {
+                const float z = (r[k] - mu_f) * inv;
+                if (z_out) __stcs(z_out + row * n_win + j, z);
+                hit(z, j);
+            }
+        }
+        return;
+    }
     float s = 0.f;
     for (int j = lane; j < n_win; j += 32) s += p[j];
     const float mu_f = warp_sum(s) / (float)n_win;
@@ -41,18 +86,10 @@ __global__ void k_detect(const float *__restrict__ P, int rows, int n_win, float
     }
     const float var = warp_sum(v) / (float)n_win;
     const float inv = var > 0.f ? 1.f / sqrtf(var) : 0.f;
-    const int b = (int)(row / n_chan), c = (int)(row % n_chan);
     for (int j = lane; j < n_win; j += 32) {
         const float z = (p[j] - mu_f) * inv;
         if (z_out) z_out[row * n_win + j] = z;
-        if (z > k_sigma) {
-            const int k = atomicAdd(n_hits, 1);
-            if (k < max_hits) {
-                hits[3 * k] = b;
-                hits[3 * k + 1] = c;
-                hits[3 * k + 2] = j;
-            }
-        }
+        hit(z, j);
     }
 }
 
