@@ -778,6 +778,60 @@ def run_serve(args):
         p.close()
 
 
+def run_peaks(args):
+    """Library GEMM rates for the dtypes whose peaks the roofline otherwise
+    derives: cuBLAS SGEMM (FP32, TF32 off: the FFMA rate the FP32 beamformer
+    is held against) and cuBLASLt FP8 E4M3 (torch._scaled_mm), with cuBLAS
+    BF16 beside them as the cross-check against the driver's figure.  Square
+    8192 GEMMs; burst = 20 back-to-back calls, sustained = a loop of about
+    `--peak-seconds` seconds.  Context only: the roofline denominators stay
+    the measured BF16 figures times the nominal dtype ratio."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda")
+    n = 8192
+    flop = 2.0 * n * n * n
+    g = torch.Generator(device="cuda")
+    g.manual_seed(21)
+    a = torch.randn((n, n), generator=g, device=dev, dtype=torch.bfloat16)
+    b = torch.randn((n, n), generator=g, device=dev, dtype=torch.bfloat16)
+
+    def rate(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return flop * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    def measure(name, fn):
+        try:
+            burst = rate(fn, 20)
+            t_one = flop / (burst * 1e12)
+            sustained = rate(fn, max(20, int(args.peak_seconds / t_one)))
+            line = {"metric": "library GEMM rate (peak context)", "dtype": name, "burst_tflops": burst,
+                    "sustained_tflops": sustained, "shape": [n, n, n]}
+        except Exception as e:   # a dtype the installed torch/cuBLAS cannot run
+            line = {"metric": "library GEMM rate (peak context)", "dtype": name, "unavailable": str(e)[:200]}
+        print(json.dumps(line), flush=True)
+
+    measure("bf16", lambda: torch.matmul(a, b))
+    allow = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a32, b32 = a.float(), b.float()
+    measure("fp32 (SGEMM, TF32 off)", lambda: torch.matmul(a32, b32))
+    torch.backends.cuda.matmul.allow_tf32 = allow
+    del a32, b32
+    a8 = a.to(torch.float8_e4m3fn)
+    b8 = b.t().contiguous().to(torch.float8_e4m3fn).t()   # column-major second operand
+    one = torch.ones((), device=dev, dtype=torch.float32)
+    measure("fp8 e4m3", lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16))
+
+
 def run_aux(args):
     """The HBM-bound kernels on the real-time chunk's sizes (32 antennas, 1024
     channels, 15625 samples, 1024 beams, T_int 64): corner turn, incoherent
@@ -853,6 +907,9 @@ def main():
                     help="weak: every rank beamforms its own chunk; strong: the chunk's channels are split over ranks")
     ap.add_argument("--batched-chan-div", type=int, default=1,
                     help="divide every job's channel count (smaller case of the same jobs, for profiling)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="cuBLAS FP32 / FP8 / BF16 GEMM rates (context for the derived FP32 and FP8 peaks)")
+    ap.add_argument("--peak-seconds", type=float, default=3.0, help="length of the sustained GEMM loop")
     ap.add_argument("--aux", action="store_true",
                     help="HBM-bound kernels (corner turn, incoherent beam, detection) on the chunk's sizes")
     ap.add_argument("--serve", action="store_true",
@@ -876,6 +933,8 @@ def main():
         run_serve(args)
     elif args.aux:
         run_aux(args)
+    elif args.peaks:
+        run_peaks(args)
     else:
         run_ours(args)
 
