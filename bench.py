@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -61,9 +62,15 @@ def peaks():
 
 
 def kernel_source_sha():
+    """Hash of the fused kernel's code (its two source files with comments and
+    blank space removed), so that a profile is invalidated by a code change
+    and not by an edit of a comment."""
     h = hashlib.sha256()
     for f in ("k_tc.cu", "ptx.cuh"):   # the kernel's own sources
-        h.update(open(os.path.join(ROOT, "paper_1412_4907_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1412_4907_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -19,20 +19,24 @@
 //   warp 1       allocates 512 TMEM columns; one thread issues tcgen05.mma,
 //                128 x NT x 16 (or x32 for FP8) per instruction, into two
 //                NT-column FP32 accumulators (the epilogue drains one while
-//                the next tile accumulates)
+//                the next tile accumulates), stepping precomputed descriptor
+//                words by one add per MMA
 //   warps 2-17   epilogue in two groups of 8 that take alternate tiles (and
 //                so alternate accumulators): while one group reads and sums a
 //                tile the other is already waiting for the next, so the
 //                accumulator's read-out and the squaring no longer sit in
 //                series with the MMA of the tile after next.  In a group, two
 //                warps per TMEM lane quarter, each on a half of the tile's
-//                columns, read with 64-column tcgen05.ld; the accumulator is
-//                handed back to the MMA before any arithmetic; then squares
+//                columns, read 64 columns at a time with tcgen05.ld and hand
+//                the accumulator back to the MMA after the last load; squares
 //                with packed FP32 FMAs, window sums in a fixed order, re+im
 //                combination via one shuffle (the two rows of a beam are 16
-//                lanes apart), window powers staged in shared memory
+//                lanes apart), window powers staged in shared memory (the
+//                staging slot is waited for after the first load, off the
+//                path between the MMA and the read-out)
 //   warp 18      store warp: writes each staged tile as one run of windows
-//                per beam (16-byte stores), four tiles in flight.
+//                per beam (16-byte stores for 4 windows, 8-byte for 2), four
+//                tiles in flight.
 // 19 warps: at most 96 registers a thread (five warps share an SM
 // sub-partition's 16K registers).
 // Work: the M tiles of a channel are split into weight groups; the CTAs are
