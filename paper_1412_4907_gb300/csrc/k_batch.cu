@@ -592,6 +592,7 @@ struct bf_batch {
     int n = 0;
     BatchCore core;
     BatchJob *h_jobs = nullptr;   // pinned, so a captured copy reads it at replay
+    std::vector<int> slot;        // job -> its row of the table (rows in order of decreasing K)
     BatchJob *d_jobs = nullptr;
     std::vector<void *> expand_buf;   // per job, FP16 copies of 8/4-bit inputs
     std::vector<size_t> expand_bytes;
@@ -645,6 +646,17 @@ bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, in
     b->plans.assign(plans, plans + n_plans);
     b->n = n_plans;
     b->core = core;
+    // The launch walks the table's rows in order.  Rows are sorted by
+    // decreasing K blocks (then by job): on the 48 uneven sub-array jobs a
+    // launch with the long-K jobs first took 80 ms against 84-86 ms in the
+    // callers' order and 87 ms with the short-K jobs first.  The order only
+    // changes which units run when; each job still writes its own outputs.
+    std::vector<int> order(n_plans);
+    for (int i = 0; i < n_plans; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return plans[x]->wf.kb > plans[y]->wf.kb; });
+    b->slot.assign(n_plans, 0);
+    for (int r = 0; r < n_plans; ++r) b->slot[order[r]] = r;
     cudaError_t e;
     if ((e = cudaHostAlloc((void **)&b->h_jobs, sizeof(BatchJob) * n_plans, cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_jobs, sizeof(BatchJob) * n_plans)) != cudaSuccess ||
@@ -695,7 +707,7 @@ bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
     BatchJob J;
     bf_status st = batch_fill_job(b->core, &J, p, xin, T, out, 0, nullptr, nullptr);
     if (st != BF_OK) return st;
-    b->h_jobs[job] = J;
+    b->h_jobs[b->slot[job]] = J;
     b->in[job] = x;
     b->n_samp[job] = T;
     b->set[job] = 1;
@@ -722,7 +734,7 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
     cudaError_t e;
     for (int j = 0; j < b->n; ++j) {
         const bf_plan *p = b->plans[j];
-        if (b->h_jobs[j].units > 0 && (p->dtype == BF_CI8 || p->dtype == BF_CI4)) {
+        if (b->h_jobs[b->slot[j]].units > 0 && (p->dtype == BF_CI8 || p->dtype == BF_CI4)) {
             e = launch_expand_to_f16(b->in[j], p->dtype, b->expand_buf[j], (long long)p->C * b->n_samp[j] * p->N,
                                      p->N, s);
             if (e != cudaSuccess) return cuda_error(e, "integer expansion");
