@@ -224,10 +224,11 @@ def test_tc_shapes(bf, n_ant, n_beam, n_samp, t_int, mode):
 def test_config3_shape_precision_modes(bf, mode):
     """The precision-sweep shape per channel (256 antennas on a 200 m random
     layout, 2048 beams, 8192 samples, T_int 64, sigma 16 + one 10 dB source)
-    on 2 of its channels: kernel error against the oracle with the same
-    stored values, and the end-to-end error against the FP64 beamformer of the
-    unquantised FP32 base voltages (recorded per mode)."""
-    scene, dirs, t_int = synth.config3(n_chan=2)
+    on 16 of its channels (the first 16 of the band's 4096, in full): kernel
+    error against the oracle with the same stored values, and the end-to-end
+    error against the FP64 beamformer of the unquantised FP32 base voltages
+    (recorded per mode)."""
+    scene, dirs, t_int = synth.config3(n_chan=16)
     x, X64 = stored_voltages(scene, mode)
     P, q = run_power(bf, scene, dirs, t_int, mode, x)
     check("config3_shape_kernel", P, oracle_power_for_mode(scene, dirs, t_int, mode, X64), mode)
@@ -496,7 +497,8 @@ def test_misaligned_pointer_rejected(bf):
 def test_config2_full_size_sampled_channels(bf):
     """The real-time FP16 workload at full size (32 antennas, 1024 channels,
     1024 beams, 15625 samples, T_int = 64) in the launch configuration the
-    benchmark times; the oracle checks 8 seeded channels in full."""
+    benchmark times; the oracle checks 16 seeded channels in full (channels
+    are independent, so this is exact parity for those outputs)."""
     scene, dirs, t_int = synth.config2()
     x = synth.voltages(scene, synth.C16F)
     plan = bf.Plan(scene.pos, scene.freqs, dirs, synth.C16F, t_int)
@@ -504,7 +506,7 @@ def test_config2_full_size_sampled_channels(bf):
     del x
     P = plan.execute(xd)
     plan.sync()
-    chans = sorted(np.random.default_rng(2).choice(1024, size=8, replace=False).tolist())
+    chans = sorted(np.random.default_rng(2).choice(1024, size=16, replace=False).tolist())
     Pg = P[:, chans, :].cpu().numpy()
     plan.close()
     del xd, P
