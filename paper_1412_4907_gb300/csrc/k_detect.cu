@@ -8,9 +8,9 @@
 // One warp per (beam, channel) row, three passes over the row (in registers
 // for rows of up to 256 windows, else re-read from L1), all in FP32 with a
 // fixed reduction order (lane-strided partial sums, then a butterfly), so
-// the result does not depend on the launch shape: the mean, then the population variance as the mean of the
-// squared deviations from it (two passes: no cancellation), then z =
-// (P - mu) / sigma compared with k.  GB300's FP64 rate is a small fraction of
+// the result does not depend on the launch shape: the mean, then the
+// population variance as the mean of the squared deviations from it (two
+// passes: no cancellation), then z = (P - mu) / sigma compared with k.  GB300's FP64 rate is a small fraction of
 // its FP32 rate, so FP64 here would make the kernel arithmetic-bound; the
 // FP32 statistics agree with the FP64 oracle to ~1e-6 relative.
 #include "bf_internal.h"
