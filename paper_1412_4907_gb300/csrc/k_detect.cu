@@ -10,9 +10,10 @@
 // fixed reduction order (lane-strided partial sums, then a butterfly), so
 // the result does not depend on the launch shape: the mean, then the
 // population variance as the mean of the squared deviations from it (two
-// passes: no cancellation), then z = (P - mu) / sigma compared with k.  GB300's FP64 rate is a small fraction of
-// its FP32 rate, so FP64 here would make the kernel arithmetic-bound; the
-// FP32 statistics agree with the FP64 oracle to ~1e-6 relative.
+// passes: no cancellation), then z = (P - mu) / sigma compared with k.
+// GB300's FP64 rate is a small fraction of its FP32 rate, so FP64 here
+// would make the kernel arithmetic-bound; the FP32 statistics agree with
+// the FP64 oracle to ~1e-6 relative.
 #include "bf_internal.h"
 
 namespace bfi {
