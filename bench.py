@@ -86,7 +86,7 @@ def profiled_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms; only the
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; only the
     samples taken inside [start, stop] of the timed region are kept."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -104,7 +104,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "100", "-f", self.path],
+                 "-i", str(self.gpu), "-lms", "50", "-f", self.path],
                 stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -356,14 +356,17 @@ def run_ours(args):
         return
 
     pk, pk_kind = peaks()
-    peak = pk["bf16_tflops_sustained"]
+    # the timed region (K steps back to back) is held against the burst peak
+    # when it lasts under a second, else against the sustained one
+    peak, peak_src, burst, sust = roofline_peak(pk, pk_kind, total_ms)
     achieved = F / (k_ms * 1e-3) / 1e12
     alg_bytes = x_host.nbytes + B * C * T_o * 4
     w_bytes = C * (B // 64) * 128 * 64 * 2
     hbm = pk["hbm_gbs"]
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(), "kernel": "k_tc (fused beamform+detect+integrate)",
-            "peak_source": f"bf16_tflops_sustained, {pk_kind} (FP16 = BF16 rate)",
+            "frac": achieved / peak, "frac_burst": achieved / burst, "frac_sustained": achieved / sust,
+            "traffic": profiled_traffic(), "kernel": "k_tc (fused beamform+detect+integrate)",
+            "peak_source": peak_src + " (FP16 = BF16 rate)", "timed_region_ms": total_ms,
             "algorithmic_bytes": alg_bytes + w_bytes,
             "hbm_frac": (alg_bytes + w_bytes) / (k_ms * 1e-3) / 1e9 / hbm}
     cpu = None
@@ -384,10 +387,32 @@ def run_ours(args):
             "breakdown_ms": {"beamform": k_ms, "weights_alone": w_ms,
                              "weights": "refreshed every chunk on a side stream, overlapped with the beamformer"},
             "fp32_form": fp32, "clocks": clk}
-    print(json.dumps(line), flush=True)
     plan.close()
+    del xd, out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    # the target forms beside the headline chunk (after it, so its buffers are free)
+    if not args.no_batched and world == 1 and not args.channels:
+        line["batched"] = batched_measure(args, emit=False)
+    if not args.no_serve and world == 1 and not args.channels:
+        line["serve"] = {f"{r:g}_chunks_per_s": serve_summary(serve_measure(args, r, args.serve_seconds, emit=False))
+                         for r in (args.serve_rate, args.serve_rate_within_link)}
+        if not args.no_fp32_form:
+            line["fp32_serve"] = fp32_serve_measure(args, args.serve_rate, args.serve_seconds, args.serve_fp32_chunks,
+                                                    emit=False)
+    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def serve_summary(r):
+    """The figures of a serving run that the headline line carries."""
+    keys = ("chunks", "rate_hz", "seconds_offered", "latency_ms", "latency_from_step_start_ms", "offered_tflops",
+            "device_tflops", "device_busy_frac", "roofline", "h2d_gbps_offered", "h2d_gbps_achieved",
+            "h2d_gbps_while_copying", "copy_in_busy_frac", "mean_chunks_per_step")
+    d = {k: r[k] for k in keys}
+    d["sustained_tflops"] = r["value"]
+    return d
 
 
 def run_sweep(args):
@@ -407,11 +432,9 @@ def run_sweep(args):
     N, B, T = scene.n_ant, dirs.shape[0], scene.n_samp
     F = flops(N, B, n_chan, T)
     pk, pk_kind = peaks()
-    bf16_peak = pk["bf16_tflops_sustained"]
     # tensor peak per operand type: FP8 runs at twice the 16-bit rate; int8 and
     # 4-bit inputs are multiplied as FP16; FP32 runs on the CUDA cores
-    peak = {synth.C16F: bf16_peak, synth.C16BF: bf16_peak, synth.C8E4M3: 2 * bf16_peak,
-            synth.CI8: bf16_peak}
+    ratio = {synth.C16F: 1.0, synth.C16BF: 1.0, synth.C8E4M3: 2.0, synth.CI8: 1.0}
     chans = [3, n_chan - 5]
     x32_sub = synth.voltages(scene, synth.C32, channels=chans).view(np.complex64).astype(np.complex128)
     sub_freqs = scene.freqs[chans]
@@ -446,12 +469,12 @@ def run_sweep(args):
         plan.close()
         del xd, out
         tf = F / (ms * 1e-3) / 1e12
+        pkm, pk_src, _, pks = roofline_peak(pk, pk_kind, ms * n, ratio.get(mode, 1.0), "FP8")
         line = {"metric": "precision sweep: fused beamform TFLOP/s and power error vs FP64", "mode": synth.MODE_NAMES[mode],
                 "value": tf, "unit": UNIT, "ms_per_launch": ms,
-                "roofline": None if mode == synth.C32 else {"bound": "tensor", "achieved": tf, "peak": peak[mode],
-                                                            "frac": tf / peak[mode], "unit": "TFLOP/s",
-                                                            "peak_source": f"bf16_tflops_sustained {pk_kind}"
-                                                                           + (" x 2 (FP8 nominal ratio)" if mode == synth.C8E4M3 else "")},
+                "roofline": None if mode == synth.C32 else {"bound": "tensor", "achieved": tf, "peak": pkm,
+                                                            "frac": tf / pkm, "frac_sustained": tf / pks,
+                                                            "unit": "TFLOP/s", "peak_source": pk_src},
                 "error_kernel": {"max_rel": kmx, "l2_rel": kl2},
                 "error_vs_fp64": {"max_rel": emx, "l2_rel": el2, "channels": chans},
                 "tiling": q, "config": {"workload": f"config-3 shape: 256 antennas, 2048 beams, 8192 samples, T_int 64, "
@@ -488,13 +511,30 @@ def config4_inputs(jobs, torch, device="cuda"):
     return xs
 
 
+def roofline_peak(pk, pk_kind, region_ms, ratio=1.0, what="BF16"):
+    """The tensor peak a measured region is held against: the burst figure for
+    a region shorter than a second (the GPU has not settled at its power
+    limit), the sustained one for longer regions; both fractions are kept."""
+    burst, sust = pk["bf16_tflops"] * ratio, pk["bf16_tflops_sustained"] * ratio
+    use_burst = region_ms < 1000.0
+    src = ("bf16_tflops (burst)" if use_burst else "bf16_tflops_sustained") + f", {pk_kind}"
+    if ratio != 1.0:
+        src += f" x {ratio:g} (nominal {what} ratio)"
+    return (burst if use_burst else sust), src, burst, sust
+
+
 def run_batched(args):
+    batched_measure(args, emit=True)
+
+
+def batched_measure(args, emit=True):
     """Config 4: 48 sub-array jobs of uneven size (N in {16..256}, B
     log-uniform in 8..4096, C in {128, 512, 2048}, T = 4096, FP16, T_int 64)
-    in one graph-captured persistent launch.  One JSON line per variant:
-    fixed 128-sample tiles, the autotuned tile width, and the jobs run one
-    plan at a time through bf_execute (each with the single-plan planner's
-    tiling); plus the power error on sampled channels against the oracle."""
+    in one graph-captured persistent launch.  Variants: fixed 128-sample
+    tiles, the autotuned tile width, and the jobs run one plan at a time
+    through bf_execute (each with the single-plan planner's tiling); plus the
+    power error on sampled channels against the oracle.  With ``emit`` one
+    JSON line per variant is printed; the summary dict is returned."""
     import torch
 
     import oracle
@@ -515,9 +555,12 @@ def run_batched(args):
     xs = config4_inputs(jobs, torch)
     torch.cuda.synchronize()
     pk, pk_kind = peaks()
-    peak = pk["bf16_tflops_sustained"]
     steps = max(3, min(args.steps, 20))
     warm = max(3, min(args.warmup, 5))
+    summary = {"workload": "48 sub-array jobs: N in {16,32,64,128,256} of the 256-antenna 200 m layout, "
+                           "B log-uniform 8..4096, C in {128,512,2048}" + (f" / {div}" if div > 1 else "")
+                           + ", T 4096 FP16, T_int 64, one graph-captured persistent launch",
+               "total_tflop": F / 1e12, "steps": steps, "warmup": warm}
 
     def timed(run):
         for _ in range(warm):
@@ -531,12 +574,18 @@ def run_batched(args):
         b.synchronize()
         return a.elapsed_time(b) / steps
 
-    def line(variant, ms, extra):
+    def line(variant, ms, extra, key):
         tf = F / (ms * 1e-3) / 1e12
+        peak, src, burst, sust = roofline_peak(pk, pk_kind, ms * steps)
+        summary[key] = {"ms_per_step": ms, "tflops": tf, "frac": tf / peak, "frac_burst": tf / burst,
+                        "frac_sustained": tf / sust, "peak_source": src,
+                        **{k: v for k, v in extra.items() if k != "tuning_table"}}
+        if not emit:
+            return
         d = {"metric": "batched uneven launch: beamform TFLOP/s", "variant": variant, "value": tf, "unit": UNIT,
              "ms_per_step": ms, "steps": steps, "warmup": warm, "dtype": "f16", "data": "synthetic",
              "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-                          "peak_source": f"bf16_tflops_sustained {pk_kind}"},
+                          "frac_sustained": tf / sust, "peak_source": src},
              "config": {"workload": "48 sub-array jobs: N in {16,32,64,128,256} of the 256-antenna 200 m layout, "
                                     "B log-uniform 8..4096, C in {128,512,2048}" + (f" / {div}" if div > 1 else "")
                                     + ", T 4096 FP16, T_int 64",
@@ -552,7 +601,7 @@ def run_batched(args):
     batch.capture()
     ms_fixed = timed(batch.replay)
     batch.sync()
-    line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": 1})
+    line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": 1}, "fixed_128")
     batch.close()
     # autotuned
     tuned = tune.tune_batch(plans, xs, outs, n_samps, stream=stream, reps=3, cache=None)
@@ -563,14 +612,15 @@ def run_batched(args):
     ms_tuned = timed(batch.replay)
     batch.sync()
     line("batched, autotuned tile", ms_tuned, {"tile_t": tuned["tile_t"], "tuning_table": tuned["table"],
-                                                "speedup_vs_fixed": ms_fixed / ms_tuned, "gpu_launches_per_step": 1})
+                                                "speedup_vs_fixed": ms_fixed / ms_tuned, "gpu_launches_per_step": 1},
+         "autotuned")
     # one plan at a time
     def per_plan():
         for p, x, o, T in zip(plans, xs, outs, n_samps):
             bf.bf_execute(p.handle, x.data_ptr(), T, o.data_ptr(), stream.cuda_stream)
     ms_seq = timed(per_plan)
     line("one launch per job (bf_execute)", ms_seq, {"gpu_launches_per_step": len(plans),
-                                                     "batched_speedup": ms_seq / ms_tuned})
+                                                     "batched_speedup": ms_seq / ms_tuned}, "one_launch_per_job")
     # parity on sampled channels of four jobs (batched, autotuned outputs)
     batch.replay()
     batch.sync()
@@ -587,8 +637,17 @@ def run_batched(args):
         mx, l2 = power_errors(outs[j][:, c:c + 1, :].cpu().numpy(), Pref)
         errs.append({"job": j, "N": p.N, "B": p.B, "channel": c, "max_rel": mx, "l2_rel": l2})
     batch.close()
-    print(json.dumps({"metric": "batched uneven launch: power error vs FP64 oracle (same FP16 inputs and weights)",
-                      "samples": errs}), flush=True)
+    summary["parity_vs_oracle"] = {"max_rel": max(e["max_rel"] for e in errs), "l2_rel": max(e["l2_rel"] for e in errs),
+                                   "jobs_sampled": len(errs)}
+    if emit:
+        print(json.dumps({"metric": "batched uneven launch: power error vs FP64 oracle (same FP16 inputs and weights)",
+                          "samples": errs}), flush=True)
+    for p in plans:
+        p.close()
+    del xs, outs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return summary
 
 
 SERVE_CONFIGS = [(32, 1024, 1024, synth.C16F), (64, 64, 4096, synth.CI8), (128, 512, 2048, synth.C16F),
@@ -640,12 +699,19 @@ def pct(a, q):
 
 
 def run_serve(args):
-    """Config 5: Poisson arrivals (default 400 chunks/s) of 0.25-1 s chunks
-    from 6 streams (32-512 antennas, 64-8192 beams, 256-4096 channels, FP16 or
-    int8), served by bf_server: latency from arrival on the host to powers in
-    host memory (p50/p99), sustained and device-only TFLOP/s; then the plain
-    FP32 single-job path (bf_execute_host, one chunk at a time) on the first
-    chunks of the same arrival list."""
+    serve_measure(args, args.serve_rate, args.serve_seconds, emit=True)
+    if not args.no_fp32_form:
+        fp32_serve_measure(args, args.serve_rate, args.serve_seconds, args.serve_fp32_chunks, emit=True)
+
+
+def serve_measure(args, rate, seconds, emit=True):
+    """Config 5: Poisson arrivals (``rate`` chunks/s for ``seconds``) of
+    0.25-1 s chunks from 6 streams (32-512 antennas, 64-8192 beams, 256-4096
+    channels, FP16 or int8), served by bf_server: latency from arrival on the
+    host to powers in host memory (p50/p99), sustained and device-only
+    TFLOP/s.  Prints one JSON line with ``emit``; returns the result dict."""
+    import threading
+
     import torch
 
     import paper_1412_4907_gb300 as bf
@@ -664,7 +730,7 @@ def run_serve(args):
     server.drain(120000)
     server.poll(64)
     base = server.stats()
-    arrivals = serve_arrivals(args.serve_rate, args.serve_seconds)
+    arrivals = serve_arrivals(rate, seconds)
     series, stop = [], [False]
 
     def sample():   # link and device counters every 0.5 s, to see the rates over the run
@@ -680,7 +746,6 @@ def run_serve(args):
                            "done": st_["completed"] - base["completed"]})
             last = st_
 
-    import threading
     t0 = bf.bf_server_now() + 0.05
     sampler = threading.Thread(target=sample, daemon=True)
     sampler.start()
@@ -725,39 +790,52 @@ def run_serve(args):
     steps = st["steps"] - base["steps"]
     sustained = F / (t_last - t0) / 1e12
     pk, pk_kind = peaks()
+    dev_tf = F / (kernel_ms * 1e-3) / 1e12
+    peak, src, burst, sust = roofline_peak(pk, pk_kind, kernel_ms)
     res = {"metric": "serving stream: p50/p99 chunk latency and sustained TFLOP/s", "value": sustained,
            "unit": UNIT, "higher_is_better": True, "dtype": "f16 (int8 inputs widened to f16)", "data": "synthetic",
-           "chunks": len(ids), "seconds_offered": args.serve_seconds, "rate_hz": args.serve_rate,
+           "chunks": len(ids), "seconds_offered": seconds, "rate_hz": rate,
            "latency_ms": {"p50": 1e3 * pct(lat, 50), "p99": 1e3 * pct(lat, 99), "mean": 1e3 * float(np.mean(lat)),
                           "max": 1e3 * float(np.max(lat))},
            "latency_from_step_start_ms": {"p50": 1e3 * pct(lat_dev, 50), "p99": 1e3 * pct(lat_dev, 99)},
            "latency_p99_ms_per_config": {str(k): 1e3 * pct(v, 99) for k, v in sorted(per_cfg.items())},
-           "offered_tflops": F / args.serve_seconds / 1e12, "device_tflops": F / (kernel_ms * 1e-3) / 1e12,
+           "offered_tflops": F / seconds / 1e12, "device_tflops": dev_tf,
            "device_busy_frac": kernel_ms * 1e-3 / (t_last - t0),
-           "roofline": {"bound": "tensor", "achieved": F / (kernel_ms * 1e-3) / 1e12, "peak": pk["bf16_tflops_sustained"],
-                        "unit": "TFLOP/s", "frac": F / (kernel_ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"],
-                        "peak_source": f"bf16_tflops_sustained {pk_kind}"},
-           "h2d_gbps_offered": h2d / args.serve_seconds / 1e9, "h2d_gbps_achieved": h2d / (t_last - t0) / 1e9,
+           "roofline": {"bound": "tensor", "achieved": dev_tf, "peak": peak, "unit": "TFLOP/s", "frac": dev_tf / peak,
+                        "frac_sustained": dev_tf / sust, "peak_source": src},
+           "h2d_gbps_offered": h2d / seconds / 1e9, "h2d_gbps_achieved": h2d / (t_last - t0) / 1e9,
            "h2d_gbps_while_copying": copy_b / (copy_ms * 1e-3) / 1e9 if copy_ms else None,
            "copy_in_busy_frac": copy_ms * 1e-3 / (t_last - t0),
            "steps": steps, "mean_chunks_per_step": len(ids) / max(1, steps), "max_chunks_per_step": st["max_jobs_per_step"],
            "arena_gb": st["arena_bytes"] / 2**30, "arena_peak_gb": st["arena_peak"] / 2**30,
            "submit_lag_s": t_sub_end - (t0 + arrivals[-1][0]) if arrivals else 0.0,
-           "series_0p5s": series,
            "config": {"workload": "6 streams (32,1024,1024,f16) (64,64,4096,i8) (128,512,2048,f16) (256,2048,512,i8) "
                                   "(512,8192,256,f16) (512,256,4096,i8) as (N,B,C,dtype); Poisson arrivals, chunk "
                                   "0.25-1 s at 1024 samples/s per channel, T_int 64 with the open window carried",
                       "tile_t": st["tile_t"], "max_steps": args.serve_steps, "arena_gib": args.serve_mem}}
-    print(json.dumps(res), flush=True)
+    if emit:
+        print(json.dumps({**res, "series_0p5s": series}), flush=True)
     for p in plans:
         p.close()
     del pools, rings
     torch.cuda.synchronize()
-    if args.no_fp32_form:
-        return
-    # the plain FP32 single-job path on the first chunks of the same list
+    torch.cuda.empty_cache()
+    return res
+
+
+def fp32_serve_measure(args, rate, seconds, n_chunks, emit=True):
+    """The plain FP32 single-job path (bf_execute_host: one chunk at a time,
+    FP32 voltages, the CUDA-core kernel) served on the first ``n_chunks``
+    arrivals of the same Poisson list, in real time: each chunk starts when
+    it has arrived and the previous one is done, and its latency runs from its
+    arrival to its powers in host memory (a FIFO single-job server)."""
+    import torch
+
+    import paper_1412_4907_gb300 as bf
+    torch.cuda.set_device(0)
+    arrivals = serve_arrivals(rate, seconds)
     plans32 = serve_plans(bf, torch.cuda.current_stream(), mode_override=synth.C32)
-    n32 = min(len(arrivals), args.serve_fp32_chunks)
+    n32 = min(len(arrivals), n_chunks)
     need = max(C * T * N for (_, cfg, T) in arrivals[:n32] for (N, _, C, _) in [SERVE_CONFIGS[cfg]])
     xh = torch.empty(2 * need, dtype=torch.float32).pin_memory()
     xh.normal_(0.0, 0.7071067811865476)
@@ -765,24 +843,33 @@ def run_serve(args):
                        dtype=torch.float32).pin_memory()
     for i in range(len(plans32)):   # warm-up
         bf.bf_execute_host(plans32[i].handle, xh.data_ptr(), 64, outh.data_ptr())
-    svc, F32 = [], 0.0
-    t_start = time.perf_counter()
-    for (_, cfg, T) in arrivals[:n32]:
+    svc, lat, F32 = [], [], 0.0
+    t0 = time.perf_counter() + 0.01
+    for (ta, cfg, T) in arrivals[:n32]:
+        due = t0 + ta
+        while time.perf_counter() < due:
+            pass
         a = time.perf_counter()
         bf.bf_execute_host(plans32[cfg].handle, xh.data_ptr(), T, outh.data_ptr())
-        svc.append(time.perf_counter() - a)
+        b = time.perf_counter()
+        svc.append(b - a)
+        lat.append(b - due)
         N, B, C, _ = SERVE_CONFIGS[cfg]
         F32 += flops(N, B, C, T)
-    busy = time.perf_counter() - t_start
-    offered32 = F32 / (arrivals[n32 - 1][0] if n32 else 1.0)
-    print(json.dumps({"metric": "serving stream: plain FP32 single-job path (bf_execute_host, one chunk at a time)",
-                      "value": F32 / busy / 1e12, "unit": UNIT, "dtype": "f32", "chunks": n32,
-                      "service_ms": {"p50": 1e3 * pct(svc, 50), "p99": 1e3 * pct(svc, 99)},
-                      "offered_tflops": offered32 / 1e12,
-                      "note": "back to back with no queueing: service time is a lower bound on its latency; "
-                              "at the offered rate its queue grows without bound when offered > value"}), flush=True)
+    busy = sum(svc)
+    res = {"metric": "serving stream: plain FP32 single-job path (bf_execute_host, one chunk at a time)",
+           "value": F32 / busy / 1e12, "unit": UNIT, "dtype": "f32", "chunks": n32, "rate_hz": rate,
+           "latency_ms": {"p50": 1e3 * pct(lat, 50), "p99": 1e3 * pct(lat, 99), "max": 1e3 * max(lat)},
+           "service_ms": {"p50": 1e3 * pct(svc, 50), "p99": 1e3 * pct(svc, 99)},
+           "offered_tflops": F32 / max(arrivals[n32 - 1][0], 1e-9) / 1e12 if n32 else 0.0,
+           "note": "the first chunks of the same arrival list; the queue grows whenever offered > value"}
+    if emit:
+        print(json.dumps(res), flush=True)
     for p in plans32:
         p.close()
+    del xh, outh
+    torch.cuda.synchronize()
+    return res
 
 
 def run_peaks(args):
@@ -925,7 +1012,11 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="seconds of arrivals")
     ap.add_argument("--serve-mem", type=float, default=96.0, help="server arena in GiB")
     ap.add_argument("--serve-steps", type=int, default=3, help="server steps in flight (1..8)")
-    ap.add_argument("--serve-fp32-chunks", type=int, default=40, help="chunks for the FP32 single-job comparison")
+    ap.add_argument("--serve-fp32-chunks", type=int, default=24, help="chunks for the FP32 single-job comparison")
+    ap.add_argument("--serve-rate-within-link", type=float, default=250.0,
+                    help="second arrival rate of the default run (within the host link's rate)")
+    ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched uneven launch")
+    ap.add_argument("--no-serve", action="store_true", help="default run: skip the serving runs")
     ap.add_argument("--channels", type=int, default=0,
                     help="run only the first C channels (same per-channel shape; for profiling)")
     args = ap.parse_args()

@@ -137,8 +137,9 @@ bf_status bf_execute(bf_plan *plan, const void *d_voltages, int n_samp,
 /*
  * bf_execute_complex — beam voltages without detection (the S-engine style
  * complex beam output of Section 1.1; also a test hook for the raw sums).
- *  d_beams  device, float [B][C][n_samp][2] (re, im).
- * Same arguments and errors as bf_execute.
+ *  d_beams  device, float [B][C][n_samp][2] (re, im), 8-byte aligned.
+ * Same arguments and errors as bf_execute (BF_ERR_ARG also for d_beams not
+ * 8-byte aligned).
  */
 bf_status bf_execute_complex(bf_plan *plan, const void *d_voltages, int n_samp,
                              float *d_beams, void *stream);
@@ -201,7 +202,10 @@ bf_status bf_plan_set_kernel(bf_plan *plan, int kernel, int tile_t);
 bf_status bf_plan_set_tiles(bf_plan *plan, int tile_t, int group_tiles, int x_stages);
 
 /* bf_plan_query_tiles — the tiling in use (any output may be NULL): tile_t,
- * group_tiles, x_stages and the number of weight groups per channel. */
+ * group_tiles, x_stages and the number of weight groups per channel.
+ * x_stages is 0 for plans whose weights are streamed (K >= 4 blocks of 128
+ * bytes per weight row): those run the batched kernel's pipeline, which sizes
+ * its own stages; set_tiles' group_tiles and x_stages do not apply to them. */
 bf_status bf_plan_query_tiles(const bf_plan *plan, int *tile_t, int *group_tiles,
                               int *x_stages, int *n_groups);
 

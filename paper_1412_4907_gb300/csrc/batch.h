@@ -38,12 +38,15 @@ struct __align__(128) BatchJob {
 struct BatchCore {
     int nt = 256, nsplit = 2, wpt = 4, t_int = 64, xst = 2, nacc = 2, smem = 0;
     bool f8 = false;
+    bool cpx = false;   // complex beams [B][C][T][2] instead of powers (single plans only)
     int num_sms = 1;
 };
 
-// Checks that the plans can share one launch (tensor-core, CTN, one operand
+// Checks that the plans can share one launch (tensor-core, one operand
 // format, one T_int, one device) and picks the tile width (tile_t = 0: the
-// widest that fits).  Sets the kernels' shared-memory attribute.
+// widest that fits).  Sets the kernels' shared-memory attribute.  The kernel
+// reads [C][T][2N] operand voltages: callers with antenna-major input corner
+// turn it first (bf_batch_create and bf_server_create accept CTN plans only).
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t);
 
 // Fills one job.  x_mma: the voltages as the MMA reads them (the FP16

@@ -20,6 +20,8 @@ bf_status set_error(bf_status s, const std::string &msg)
     return s;
 }
 
+void clear_error() { g_last_error.clear(); }
+
 bf_status cuda_error(cudaError_t e, const char *what)
 {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -359,10 +361,11 @@ static bf_status run_range_body(bf_plan *p, const void *x, int c_base, int c_lau
         BF_CUDA(launch_expand_to_f16(xin, p->dtype, scr, (long long)n_samp, p->N, s), "integer expansion");
         xin = scr;
     }
-    if (mode == 0 && p->tc.stream) {
+    if (p->tc.stream) {
         // large antenna counts: the batched kernel's streamed pipeline with one
         // job (its CTAs walk neighbouring tiles of one channel together, so the
-        // weight and voltage tiles are shared in L2)
+        // weight and voltage tiles are shared in L2), for powers and for
+        // complex beams
         if (!p->bcore) {
             BatchCore core;
             bf_plan *const one[1] = {p};
@@ -370,10 +373,12 @@ static bf_status run_range_body(bf_plan *p, const void *x, int c_base, int c_lau
             if (st != BF_OK) return st;
             p->bcore = new BatchCore(core);
         }
+        BatchCore core = *p->bcore;
+        core.cpx = mode == 1;
         BatchJob J;
-        bf_status st = batch_fill_job(*p->bcore, &J, p, xin, T, out, 0, nullptr, nullptr, c_base, c_launch);
+        bf_status st = batch_fill_job(core, &J, p, xin, T, out, 0, nullptr, nullptr, c_base, c_launch);
         if (st != BF_OK) return st;
-        BF_CUDA(batch_core_launch_one(*p->bcore, J, p->d_err, s), "tensor-core kernel (streamed)");
+        BF_CUDA(batch_core_launch_one(core, J, p->d_err, s), "tensor-core kernel (streamed)");
         return BF_OK;
     }
     TcArgs ta;
@@ -438,6 +443,7 @@ bf_status bf_execute_complex(bf_plan *p, const void *x, int T, float *out, void 
     bool noop;
     bf_status st = exec_checks(p, x, T, out, 1, &noop);
     if (st != BF_OK || noop) return st;
+    if ((uintptr_t)out & 7) return set_error(BF_ERR_ARG, "complex beams must be 8-byte aligned (float pairs)");
     return run_range(p, x, 0, p->C, T, out, 1, stream ? (cudaStream_t)stream : p->stream);
 }
 

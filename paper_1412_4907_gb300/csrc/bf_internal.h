@@ -64,6 +64,7 @@ struct TcArgs {
 };
 
 bf_status set_error(bf_status s, const std::string &msg);
+void clear_error();   // every entry point starts with this: bf_last_error() then describes this call only
 bf_status cuda_error(cudaError_t e, const char *what);
 
 }  // namespace bfi

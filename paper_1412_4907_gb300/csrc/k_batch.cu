@@ -111,14 +111,17 @@ struct UnitWalk {
 // to the accumulator read-out).
 struct __align__(16) TileDesc {
     const float *wscale;   // per-beam power scale rows of the job's first channel, or NULL
-    float *out;            // the job's powers, offset to its first channel
+    const float *wsig;     // per-beam amplitude scale rows, offset likewise (complex output)
+    float *out;            // the job's powers (or complex beams), offset to its first channel
     const float *acc_in;   // carried-window sums, offset likewise, or NULL
     float *acc_out;
-    int b0, n_beams, b_pad, c, tt, T_o, c_total, last;   // last != 0: no more tiles
+    int b0, n_beams, b_pad, c, tt, T, T_o, c_total, last;   // last != 0: no more tiles
 };
 constexpr int kDescRing = 16;
 
-template <bool F8, int WIN>
+// CPX: complex beams [B][C][T][2] straight from the epilogue (the store warp
+// only recycles the descriptor slots); otherwise integrated powers.
+template <bool F8, int WIN, bool CPX>
 __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_constant__ ParamJobs pj)
 {
     const BatchJob *jobs = a.jobs ? a.jobs : pj.j;   // a table in device memory, or jobs passed by value
@@ -208,7 +211,9 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
                     t_shift = J.t_shift;
                     c_base = J.c_base;
                     d.wscale = J.wscale ? J.wscale + (size_t)J.c_base * J.b_pad : nullptr;
-                    d.out = J.out + (size_t)J.c_base * J.T_o;
+                    d.wsig = J.wsig + (size_t)J.c_base * J.b_pad;
+                    d.out = J.out + (size_t)J.c_base * (CPX ? 2 * (size_t)J.T : (size_t)J.T_o);
+                    d.T = J.T;
                     d.acc_in = J.acc_in ? J.acc_in + J.c_base : nullptr;
                     d.acc_out = J.acc_out ? J.acc_out + J.c_base : nullptr;
                     d.n_beams = J.B;
@@ -332,6 +337,17 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
             const uint32_t tempty = b_tempty + 8 * acc;
             if (!active) {
                 tile_release(tempty, lane);
+            } else if (CPX) {
+                struct {
+                    int nt, T, c_total, b_pad;
+                    const float *wsig;
+                    float *out;
+                } o{a.nt, D.T, D.c_total, D.b_pad, D.wsig, D.out};
+                const int b = D.b0 + bq;
+                epi_complex_tile(o, taddr, cols, col0, D.tt, lane, b, b < D.n_beams, D.c);
+                tile_release(tempty, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_sfull + 8 * sb);   // done with the descriptor
             } else {
                 struct {
                     int t_int, b_pad;
@@ -351,9 +367,11 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
             if (D.last) break;
             const uint32_t sb = kt % kStageDepth;
             if (!mbar_wait(b_sfull + 8 * sb, (kt / kStageDepth) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
-            const TileOut o{a.nt,    a.nsplit, a.wpt, a.t_int, 0, D.T_o, D.n_beams, D.b_pad, D.c_total,
-                            D.wscale, nullptr,  D.out, D.acc_in, D.acc_out};
-            store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), D.b0, D.c, D.tt, lane);
+            if (!CPX) {
+                const TileOut o{a.nt,     a.nsplit, a.wpt, a.t_int, 0,        D.T_o,    D.n_beams,
+                                D.b_pad,  D.c_total, D.wscale, nullptr, D.out, D.acc_in, D.acc_out};
+                store_tile(o, stage + sb * (kBeamsPerMTile * kMaxWinPerTile), D.b0, D.c, D.tt, lane);
+            }
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive_relaxed(b_sempty + 8 * sb);
@@ -385,16 +403,16 @@ static int batch_layout_end(int xst, int nt)
 
 // The attribute is a per-kernel maximum shared by every batch: it is set to
 // the largest size any batch asks for, so one batch never lowers another's.
-template <bool F8, int WIN>
+template <bool F8, int WIN, bool CPX>
 static cudaError_t batch_attr()
 {
-    return cudaFuncSetAttribute(k_tc_batch<F8, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    return cudaFuncSetAttribute(k_tc_batch<F8, WIN, CPX>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
 }
 
-template <bool F8, int WIN>
+template <bool F8, int WIN, bool CPX>
 static cudaError_t batch_launch(const BatchArgs &ka, const ParamJobs &pj, int grid, int smem, cudaStream_t s)
 {
-    k_tc_batch<F8, WIN><<<grid, kTcThreads, smem, s>>>(ka, pj);
+    k_tc_batch<F8, WIN, CPX><<<grid, kTcThreads, smem, s>>>(ka, pj);
     return cudaGetLastError();
 }
 
@@ -403,30 +421,44 @@ static int batch_win(int t_int)
     return (t_int == 64 || t_int == 32 || t_int == 16) ? t_int : (t_int % 16 == 0 ? 0 : -1);
 }
 
-#define BF_BATCH_DISPATCH(CORE, CALL)                            \
-    do {                                                         \
-        const int win_ = batch_win((CORE).t_int);                \
-        if ((CORE).f8) {                                         \
-            switch (win_) {                                      \
-            case 64: e = CALL(true, 64); break;                  \
-            case 32: e = CALL(true, 32); break;                  \
-            case 16: e = CALL(true, 16); break;                  \
-            case 0: e = CALL(true, 0); break;                    \
-            default: e = CALL(true, -1); break;                  \
-            }                                                    \
-        } else {                                                 \
-            switch (win_) {                                      \
-            case 64: e = CALL(false, 64); break;                 \
-            case 32: e = CALL(false, 32); break;                 \
-            case 16: e = CALL(false, 16); break;                 \
-            case 0: e = CALL(false, 0); break;                   \
-            default: e = CALL(false, -1); break;                 \
-            }                                                    \
-        }                                                        \
-    } while (0)
+// Calls F.template run<F8, WIN, CPX>() for the core's operand format, window
+// specialisation and output kind.
+template <class F>
+static cudaError_t batch_dispatch(const BatchCore &core, F &&f)
+{
+    if (core.cpx) return core.f8 ? f.template run<true, 0, true>() : f.template run<false, 0, true>();
+    const int win = batch_win(core.t_int);
+    if (core.f8) {
+        switch (win) {
+        case 64: return f.template run<true, 64, false>();
+        case 32: return f.template run<true, 32, false>();
+        case 16: return f.template run<true, 16, false>();
+        case 0: return f.template run<true, 0, false>();
+        default: return f.template run<true, -1, false>();
+        }
+    }
+    switch (win) {
+    case 64: return f.template run<false, 64, false>();
+    case 32: return f.template run<false, 32, false>();
+    case 16: return f.template run<false, 16, false>();
+    case 0: return f.template run<false, 0, false>();
+    default: return f.template run<false, -1, false>();
+    }
+}
 
-#define BF_ATTR(F, W) batch_attr<F, W>()
-#define BF_LAUNCH(F, W) batch_launch<F, W>(ka, pj, grid, core.smem, s)
+struct BatchAttr {
+    template <bool F8, int WIN, bool CPX>
+    cudaError_t run() const { return batch_attr<F8, WIN, CPX>(); }
+};
+
+struct BatchLaunch {
+    const BatchArgs &ka;
+    const ParamJobs &pj;
+    int grid, smem;
+    cudaStream_t s;
+    template <bool F8, int WIN, bool CPX>
+    cudaError_t run() const { return batch_launch<F8, WIN, CPX>(ka, pj, grid, smem, s); }
+};
 
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t)
 {
@@ -437,7 +469,6 @@ bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int til
         const bf_plan *p = plans[i];
         if (!p) return set_error(BF_ERR_ARG, "NULL plan");
         if (p->wf.simt) return set_error(BF_ERR_UNSUPPORTED, "batches run tensor-core plans (not BF_C32)");
-        if (p->layout != BF_LAYOUT_CTN) return set_error(BF_ERR_UNSUPPORTED, "batches take the CTN layout");
         if (p->wf.op != p0->wf.op)
             return set_error(BF_ERR_UNSUPPORTED, "all plans of a batch must share the operand format");
         if (p->t_int != p0->t_int) return set_error(BF_ERR_UNSUPPORTED, "all plans of a batch must share T_int");
@@ -472,8 +503,12 @@ bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int til
     c.smem = std::max(batch_layout_end(c.xst, nt), 116 * 1024);
     if (c.xst < 2 || batch_layout_end(c.xst, nt) > c.smem || c.smem > kSmemLimit)
         return set_error(BF_ERR_UNSUPPORTED, "batch stages do not fit in shared memory");
-    cudaError_t e;
-    BF_BATCH_DISPATCH(c, BF_ATTR);
+    cudaError_t e = batch_dispatch(c, BatchAttr{});
+    if (e == cudaSuccess) {   // the complex-output variant of the same format (single plans)
+        BatchCore cc = c;
+        cc.cpx = true;
+        e = batch_dispatch(cc, BatchAttr{});
+    }
     if (e != cudaSuccess) return cuda_error(e, "batch kernel attribute");
     *core = c;
     return BF_OK;
@@ -482,6 +517,8 @@ bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int til
 bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, const void *x_mma, int T,
                          float *out, int t_shift, const float *acc_in, float *acc_out, int c_base, int c_count)
 {
+    if (core.cpx && (t_shift || acc_in || acc_out))
+        return set_error(BF_ERR_ARG, "complex beam output carries no integration window");
     if (c_count < 0) c_count = p->C - c_base;
     if (c_base < 0 || c_count < 0 || c_base + c_count > p->C) return set_error(BF_ERR_ARG, "channel range");
     if (T < 0) return set_error(BF_ERR_ARG, "n_samp must be >= 0");
@@ -494,7 +531,8 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
     J->C = c_count;
     J->c_base = c_base;
     J->c_total = p->C;
-    J->t_tiles = ((T_o + partial) * p->t_int + core.nt - 1) / core.nt;
+    // complex beams: every sample; powers: the samples of whole (and carried-out) windows
+    J->t_tiles = core.cpx ? (T + core.nt - 1) / core.nt : ((T_o + partial) * p->t_int + core.nt - 1) / core.nt;
     J->mt = f.m_pad / kRowsPerMTile;
     J->kb = f.kb;
     J->ke = f.ke;
@@ -514,7 +552,8 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
     J->out = out;
     J->acc_in = t_shift > 0 ? acc_in : nullptr;
     J->acc_out = partial ? acc_out : nullptr;
-    J->units = (T_o + partial) > 0 ? (long long)c_count * J->t_tiles * J->mt : 0;
+    const bool work = core.cpx ? T > 0 : (T_o + partial) > 0;
+    J->units = work ? (long long)c_count * J->t_tiles * J->mt : 0;
     if (J->units > 0) {
         if (T == 0) {   // nothing to read: the carried sum passes straight through
             J->units = 0;
@@ -555,9 +594,7 @@ static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, co
     ka.stage_bytes = (uint32_t)batch_stage_bytes(core.nt);
     ka.err = d_err;
     const int grid = (int)std::min<long long>(core.num_sms, total_units);
-    cudaError_t e;
-    BF_BATCH_DISPATCH(core, BF_LAUNCH);
-    return e;
+    return batch_dispatch(core, BatchLaunch{ka, pj, grid, core.smem, s});
 }
 
 cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
@@ -634,11 +671,15 @@ extern "C" {
 
 bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, int tile_t)
 {
+    clear_error();
     if (!out) return set_error(BF_ERR_ARG, "out is NULL");
     *out = nullptr;
-    for (int i = 0; plans && i < n_plans; ++i)   // the batch keeps the plans' weight pointers
-        if (plans[i] && plans[i]->wbufs != 1)
+    for (int i = 0; plans && i < n_plans; ++i) {
+        if (plans[i] && plans[i]->layout != BF_LAYOUT_CTN)   // the kernel reads [C][T][N] voltages as given
+            return set_error(BF_ERR_UNSUPPORTED, "batches take the CTN layout");
+        if (plans[i] && plans[i]->wbufs != 1)   // the batch keeps the plans' weight pointers
             return set_error(BF_ERR_UNSUPPORTED, "plans with double-buffered weights cannot join a batch");
+    }
     BatchCore core;
     bf_status st = batch_core_init(&core, plans, n_plans, tile_t);
     if (st != BF_OK) return st;
@@ -677,6 +718,7 @@ bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, in
 
 bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
 {
+    clear_error();
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     if (job < 0 || job >= b->n) return set_error(BF_ERR_ARG, "job index out of range");
     if (T < 0) return set_error(BF_ERR_ARG, "n_samp must be >= 0");
@@ -724,6 +766,7 @@ bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
 
 bf_status bf_batch_execute(bf_batch *b, void *stream)
 {
+    clear_error();
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     for (int j = 0; j < b->n; ++j)
         if (!b->set[j]) return set_error(BF_ERR_STATE, "every job needs bf_batch_set before execute");
@@ -753,6 +796,7 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
 
 bf_status bf_batch_capture(bf_batch *b, void *stream)
 {
+    clear_error();
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     if (!stream) return set_error(BF_ERR_ARG, "capture needs a non-default stream");
     cudaStream_t s = (cudaStream_t)stream;
@@ -780,6 +824,7 @@ bf_status bf_batch_capture(bf_batch *b, void *stream)
 
 bf_status bf_batch_replay(bf_batch *b, void *stream)
 {
+    clear_error();
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     if (!b->graph_exec) return set_error(BF_ERR_STATE, "no captured step (bf_batch_capture first)");
     cudaError_t e = cudaGraphLaunch(b->graph_exec, (cudaStream_t)stream);
@@ -791,6 +836,7 @@ bf_status bf_batch_replay(bf_batch *b, void *stream)
 
 bf_status bf_batch_sync(bf_batch *b)
 {
+    clear_error();
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     cudaError_t e = b->launched ? cudaStreamSynchronize(b->last_stream) : cudaSuccess;
     if (e != cudaSuccess) return cuda_error(e, "batch synchronize");
@@ -806,6 +852,7 @@ bf_status bf_batch_sync(bf_batch *b)
 
 bf_status bf_batch_query(const bf_batch *b, int *tile_t, long long *units, double *flops)
 {
+    clear_error();
     if (!b) return set_error(BF_ERR_ARG, "batch is NULL");
     if (tile_t) *tile_t = b->core.nt;
     if (units) *units = b->total_units;
@@ -815,6 +862,7 @@ bf_status bf_batch_query(const bf_batch *b, int *tile_t, long long *units, doubl
 
 bf_status bf_batch_destroy(bf_batch *b)
 {
+    clear_error();
     batch_free(b);
     return BF_OK;
 }

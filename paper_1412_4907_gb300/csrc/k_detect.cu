@@ -101,6 +101,7 @@ using namespace bfi;
 extern "C" bf_status bf_detect(const float *d_power, int n_beam, int n_chan, int n_win, float k_sigma, float *d_z,
                                int *d_hits, int max_hits, int *d_n_hits, void *stream)
 {
+    clear_error();
     if (n_beam < 0 || n_chan < 0 || n_win < 0 || max_hits < 0) return set_error(BF_ERR_ARG, "negative size");
     if (!d_n_hits) return set_error(BF_ERR_ARG, "d_n_hits is NULL");
     if (max_hits > 0 && !d_hits) return set_error(BF_ERR_ARG, "d_hits is NULL");

@@ -33,6 +33,7 @@ using namespace bfi;
 
 extern "C" bf_status bf_selftest_timeout(double limit_ms, void *stream)
 {
+    clear_error();
     if (!(limit_ms > 0.0) || limit_ms > 10000.0) return set_error(BF_ERR_ARG, "limit_ms must be in (0, 10000]");
     int dev = 0, khz = 0;
     cudaError_t e = cudaGetDevice(&dev);

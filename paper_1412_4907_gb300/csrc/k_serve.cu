@@ -510,15 +510,19 @@ double bf_server_now(void) { return now_s(); }
 bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs, size_t mem_bytes, int max_steps,
                            int tile_t)
 {
+    clear_error();
     if (!out) return set_error(BF_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (max_steps < 1 || max_steps > 8) return set_error(BF_ERR_ARG, "max_steps must be in 1..8");
     if (mem_bytes < 4096) return set_error(BF_ERR_ARG, "memory budget too small");
     if (n_configs > kParamJobs)
         return set_error(BF_ERR_UNSUPPORTED, "a server takes at most " + std::to_string(kParamJobs) + " streams");
-    for (int i = 0; plans && i < n_configs; ++i)
+    for (int i = 0; plans && i < n_configs; ++i) {
+        if (plans[i] && plans[i]->layout != BF_LAYOUT_CTN)   // chunks arrive in the [C][T][N] packet order
+            return set_error(BF_ERR_UNSUPPORTED, "servers take the CTN layout");
         if (plans[i] && plans[i]->wbufs != 1)
             return set_error(BF_ERR_UNSUPPORTED, "plans with double-buffered weights cannot join a server");
+    }
     BatchCore core;
     bf_status st = batch_core_init(&core, plans, n_configs, tile_t);
     if (st != BF_OK) return st;
@@ -572,6 +576,7 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
 bf_status bf_server_submit(bf_server *s, int config, const void *h_voltages, int n_samp, float *h_power,
                            long long *id)
 {
+    clear_error();
     if (!s) return set_error(BF_ERR_ARG, "server is NULL");
     if (config < 0 || config >= (int)s->streams.size()) return set_error(BF_ERR_ARG, "config out of range");
     if (n_samp < 1) return set_error(BF_ERR_ARG, "a chunk needs at least one sample");
@@ -605,6 +610,7 @@ bf_status bf_server_submit(bf_server *s, int config, const void *h_voltages, int
 
 bf_status bf_server_poll(bf_server *s, bf_completion *out, int max, int *n_out, int timeout_ms)
 {
+    clear_error();
     if (!s || !n_out || (max > 0 && !out)) return set_error(BF_ERR_ARG, "NULL argument");
     *n_out = 0;
     std::unique_lock<std::mutex> lock(s->mu);
@@ -632,6 +638,7 @@ bf_status bf_server_poll(bf_server *s, bf_completion *out, int max, int *n_out, 
 
 bf_status bf_server_drain(bf_server *s, int timeout_ms)
 {
+    clear_error();
     if (!s) return set_error(BF_ERR_ARG, "server is NULL");
     std::unique_lock<std::mutex> lock(s->mu);
     const bool ok = s->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms), [&] {
@@ -644,6 +651,7 @@ bf_status bf_server_drain(bf_server *s, int timeout_ms)
 
 bf_status bf_server_pause(bf_server *s, int paused)
 {
+    clear_error();
     if (!s) return set_error(BF_ERR_ARG, "server is NULL");
     {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -655,6 +663,7 @@ bf_status bf_server_pause(bf_server *s, int paused)
 
 bf_status bf_server_stats(bf_server *s, bf_server_counters *out)
 {
+    clear_error();
     if (!s || !out) return set_error(BF_ERR_ARG, "NULL argument");
     std::lock_guard<std::mutex> lock(s->mu);
     out->submitted = s->submitted;
@@ -673,6 +682,7 @@ bf_status bf_server_stats(bf_server *s, bf_server_counters *out)
 
 bf_status bf_server_destroy(bf_server *s)
 {
+    clear_error();
     if (!s) return BF_OK;
     server_free(s);
     return BF_OK;

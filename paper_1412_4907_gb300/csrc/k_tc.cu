@@ -31,12 +31,14 @@
 //                the accumulator back to the MMA after the last load; squares
 //                with packed FP32 FMAs, window sums in a fixed order, re+im
 //                combination via one shuffle (the two rows of a beam are 16
-//                lanes apart), window powers staged in shared memory (the
-//                staging slot is waited for after the first load, off the
-//                path between the MMA and the read-out)
-//   warp 18      store warp: writes each staged tile as one run of windows
-//                per beam (16-byte stores for 4 windows, 8-byte for 2), four
-//                tiles in flight.
+//                lanes apart).  With 256-sample tiles and T_int of 16, 32 or
+//                64 each warp stores its windows straight to the output
+//                (direct path: nothing between the two loads but the squares
+//                of the first); otherwise the window powers are staged in
+//                shared memory for
+//   warp 18      the store warp, which writes each staged tile as one run of
+//                windows per beam (16-byte stores for 4 windows, 8-byte for
+//                2), four tiles in flight.
 // 19 warps: at most 96 registers a thread (five warps share an SM
 // sub-partition's 16K registers).
 // Work: the M tiles of a channel are split into weight groups; the CTAs are
@@ -58,7 +60,7 @@
 
 namespace bfi {
 
-constexpr int kEpiWarps = 16;               // two groups of 8, taking alternate tiles
+constexpr int kEpiWarps = 16;                      // two groups of 8, taking alternate tiles
 constexpr int kStoreWarp = 2 + kEpiWarps;          // drains the staged window powers
 constexpr int kTcThreads = (3 + kEpiWarps) * 32;
 constexpr int kStageDepth = 4;                     // staged tiles in flight
@@ -147,9 +149,9 @@ __device__ __forceinline__ float sumsq_pk(const uint32_t *r)
 
 // WIN: 16, 32 or 64 = T_int known at compile time; 0 = any multiple of 16;
 // -1 = any T_int (per-column window counter).
-// STREAM: weights are not resident; every pipeline stage carries one 64-column
-// K block of the weight tile and of the voltage tile (large antenna counts).
-template <bool F8, int WIN, bool COMPLEX, bool STREAM>
+// Plans whose weights do not fit in shared memory (K >= 4 blocks) run the
+// batched kernel's streamed pipeline instead (k_batch.cu).
+template <bool F8, int WIN, bool COMPLEX, bool DIRECT>
 __global__ void __maxnreg__(96)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
 {
@@ -184,7 +186,7 @@ __global__ void __maxnreg__(96)
         }
         for (int i = 0; i < a.nacc; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
-            mbar_init(b_tempty + 8 * i, kEpiWarps / 2);   // one group releases each use
+            mbar_init(b_tempty + 8 * i, 8);   // the 8 warps of one group release each use
         }
         mbar_init(b_drain, 1);
         for (int s = 0; s < a.gmax; ++s) {
@@ -214,92 +216,7 @@ __global__ void __maxnreg__(96)
     const long long ct1 = a.ct_total * (set + 1) / n_sets;
     const int c_first = (int)(ct0 / a.t_tiles), tt_first = (int)(ct0 % a.t_tiles);
 
-    if (warp == 0 && STREAM) {
-        // ----------------------------------------------- producer, streamed weights
-        if (lane == 0) {
-            uint32_t cnt = 0, issued = 0;
-            int st = 0;
-            bool ok = true;
-            for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
-                int m0, gs;
-                group_tiles(a, g, m0, gs);
-                int c = c_first, tt = tt_first;
-                for (long long ct = ct0; ct < ct1 && ok; ++ct) {
-                    for (int s = 0; s < gs && ok; ++s)
-                        for (int kb = 0; kb < a.kb; ++kb) {
-                            if (!mbar_wait(b_xempty + 8 * st, ((cnt >> st) & 1u) ^ 1u, abort_flag, a.err,
-                                           kWaitLimitCycles)) {
-                                ok = false;
-                                break;
-                            }
-                            cnt ^= 1u << st;
-                            issued |= 1u << st;
-                            const uint32_t dst = sx + st * a.x_stage_bytes;
-                            mbar_arrive_expect_tx(b_xfull + 8 * st, a.x_stage_bytes);
-                            tma_load_3d(dst, &wmap, b_xfull + 8 * st, kb * a.ke, (m0 + s) * kRowsPerMTile,
-                                        a.c_base + c);
-                            tma_load_3d(dst + 16384, &xmap, b_xfull + 8 * st, kb * a.ke, tt * a.nt, c);
-                            if (++st == a.xst) st = 0;
-                        }
-                    if (++tt == a.t_tiles) {
-                        tt = 0;
-                        ++c;
-                    }
-                }
-            }
-            if (*abort_flag)
-                for (int i = 0; i < a.xst; ++i)
-                    if (issued & (1u << i)) drain_wait(b_xfull + 8 * i, ((cnt >> i) & 1u) ^ 1u);
-        }
-        __syncwarp();
-    } else if (warp == 1 && STREAM) {
-        // ---------------------------------------------- MMA issuer, streamed weights
-        if (lane == 0) {
-            uint32_t par = 0, tpar = 0;
-            int st = 0, acc = 0;
-            bool ok = true;
-            for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
-                int m0, gs;
-                group_tiles(a, g, m0, gs);
-                (void)m0;
-                for (long long ct = ct0; ct < ct1 && ok; ++ct)
-                    for (int s = 0; s < gs && ok; ++s) {
-                        if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err,
-                                       kWaitLimitCycles)) {
-                            ok = false;
-                            break;
-                        }
-                        tpar ^= 1u << acc;
-                        tc_fence_after();
-                        const uint32_t d = tmem + acc * a.nt;
-                        for (int kb = 0; kb < a.kb; ++kb) {
-                            if (!mbar_wait(b_xfull + 8 * st, (par >> st) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
-                                ok = false;
-                                break;
-                            }
-                            par ^= 1u << st;
-                            tc_fence_after();
-                            const uint32_t base_w = sx + st * a.x_stage_bytes;
-#pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
-                                const uint64_t ad = sdesc_sw128(base_w + ks * 32);
-                                const uint64_t bd = sdesc_sw128(base_w + 16384 + ks * 32);
-                                if (F8) mma_f8(d, ad, bd, a.idesc, (kb | ks) != 0);
-                                else mma_f16(d, ad, bd, a.idesc, (kb | ks) != 0);
-                            }
-                            mma_commit(b_xempty + 8 * st);
-                            if (++st == a.xst) st = 0;
-                        }
-                        if (!ok) break;
-                        mma_commit(b_tfull + 8 * acc);
-                        if (++acc == a.nacc) acc = 0;
-                    }
-            }
-            mma_commit(b_drain);
-            drain_wait(b_drain, 0);
-        }
-        __syncwarp();
-    } else if (warp == 0) {
+    if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t xcnt = 0, wcnt = 0, x_issued = 0, w_issued = 0;
@@ -417,6 +334,103 @@ __global__ void __maxnreg__(96)
             drain_wait(b_drain, 0);
         }
         __syncwarp();
+    } else if (warp < kStoreWarp && DIRECT) {
+        // ---------------------------------------------- epilogue, direct stores
+        // Power output with T_int = W in {16, 32, 64} and 256-sample tiles.
+        // Warp h of a lane quarter reads its 128 columns (128h..) in two
+        // 64-column loads, hands the accumulator back to the MMA after the
+        // second, sums the squares of each window, combines the re and im rows
+        // with one shuffle and stores its windows straight to the output (one
+        // 8- or 16-byte store per beam).  With no staging buffer between the
+        // loads the accumulator returns ~40% sooner than through the staged
+        // path, which is what bounds the tile rate at 32 antennas (K = 64).
+        constexpr int W = WIN > 0 ? WIN : 64;
+        constexpr int NW = 64 / W;                    // windows per 64-column load
+        const int e = warp - 2;
+        const int grp = e >> 3;                       // this group takes the tiles with kt % 2 == grp
+        const int q = warp & 3;                       // TMEM lane quarter
+        const int h = (e & 7) >> 2;
+        const int bq = q * 16 + (lane & 15);          // beam within the M tile
+        const bool re_lane = lane < 16;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + h * 128;
+        const int jA = (h * 128) / W, jB = (h * 128 + 64) / W;   // first window of each load
+        // NW-window runs are NW-aligned in the output (vector stores need the pointer aligned too)
+        const bool vec_ok = (a.T_o % NW) == 0 && ((uintptr_t)a.out & (4 * NW - 1)) == 0;
+        const bool pair_ok = (a.T_o % 2) == 0 && ((uintptr_t)a.out & 7) == 0;   // W = 64: windows jA, jA + 1
+        uint32_t tpar = 0, kt = 0;
+        int acc = 0;
+        bool ok = true;
+        for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
+            int m0, gs;
+            group_tiles(a, g, m0, gs);
+            int c = c_first, tt = tt_first;
+            for (long long ct = ct0; ct < ct1 && ok; ++ct) {
+                const int cg = a.c_base + c;
+                const int j0 = tt * a.wpt;
+                for (int s = 0; s < gs; ++s, ++kt) {
+                    if ((int)(kt & 1u) != grp) {   // the other group's tile
+                        if (++acc == a.nacc) acc = 0;
+                        continue;
+                    }
+                    if (!mbar_wait(b_tfull + 8 * acc, (tpar >> acc) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                        ok = false;
+                        break;
+                    }
+                    tpar ^= 1u << acc;
+                    tc_fence_after();
+                    const uint32_t ta = lane_base + acc * 256;
+                    float pa[NW], pb[NW];
+                    {
+                        uint32_t r[64];
+                        tmem_ld64r(ta, r);
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) pa[k] = sumsq_pk<W>(r + k * W);
+                    }
+                    {
+                        uint32_t r[64];
+                        tmem_ld64r(ta + 64, r);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_relaxed(b_tempty + 8 * acc);
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) pb[k] = sumsq_pk<W>(r + k * W);
+                    }
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        pa[k] += __shfl_xor_sync(0xffffffffu, pa[k], 16);
+                        pb[k] += __shfl_xor_sync(0xffffffffu, pb[k], 16);
+                    }
+                    const int b = (m0 + s) * kBeamsPerMTile + bq;
+                    if (re_lane && b < a.B) {
+                        const float sc = a.wscale ? a.wscale[(size_t)cg * a.b_pad + b] : 1.f;
+                        float *o = a.out + ((size_t)b * a.c_total + cg) * a.T_o + j0;
+                        const int nA = a.T_o - (j0 + jA), nB = a.T_o - (j0 + jB);   // windows left
+                        if (NW == 1 && pair_ok && nB >= 1) {
+                            *reinterpret_cast<float2 *>(o + jA) = make_float2(pa[0] * sc, pb[0] * sc);
+                        } else if (NW == 4 && vec_ok && nB >= 4) {
+                            *reinterpret_cast<float4 *>(o + jA) = make_float4(pa[0] * sc, pa[1 % NW] * sc,
+                                                                              pa[2 % NW] * sc, pa[3 % NW] * sc);
+                            *reinterpret_cast<float4 *>(o + jB) = make_float4(pb[0] * sc, pb[1 % NW] * sc,
+                                                                              pb[2 % NW] * sc, pb[3 % NW] * sc);
+                        } else if (NW == 2 && vec_ok && nB >= 2) {
+                            *reinterpret_cast<float2 *>(o + jA) = make_float2(pa[0] * sc, pa[1 % NW] * sc);
+                            *reinterpret_cast<float2 *>(o + jB) = make_float2(pb[0] * sc, pb[1 % NW] * sc);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < NW; ++k) {
+                                if (k < nA) o[jA + k] = pa[k] * sc;
+                                if (k < nB) o[jB + k] = pb[k] * sc;
+                            }
+                        }
+                    }
+                    if (++acc == a.nacc) acc = 0;
+                }
+                if (++tt == a.t_tiles) {
+                    tt = 0;
+                    ++c;
+                }
+            }
+        }
     } else if (warp < kStoreWarp) {
         // -------------------------------------------------------------- epilogue
         const int e = warp - 2;
@@ -565,13 +579,13 @@ __global__ void __maxnreg__(96)
                 }
             }
         }
-    } else if (warp == kStoreWarp && !COMPLEX) {
+    } else if (warp == kStoreWarp && !COMPLEX && !DIRECT) {
         // ------------------------------------------------------------ store warp
         // writes each staged tile as one run of windows per beam
         uint32_t kt = 0;
         bool ok = true;
-        const bool vec = (a.T_o & 3) == 0 && (a.wpt & 3) == 0;
-        const bool vec2 = (a.T_o & 1) == 0 && (a.wpt & 1) == 0;
+        const bool vec = (a.T_o & 3) == 0 && (a.wpt & 3) == 0 && ((uintptr_t)a.out & 15) == 0;
+        const bool vec2 = (a.T_o & 1) == 0 && (a.wpt & 1) == 0 && ((uintptr_t)a.out & 7) == 0;
         for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
             int m0, gs;
             group_tiles(a, g, m0, gs);
@@ -667,17 +681,17 @@ static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * 16
 // holder and abort flag).
 static size_t layout_end(const TcConfig &c, int kb)
 {
-    const size_t x_stage = c.stream ? (size_t)(16384 + c.nt * 128) : (size_t)kb * c.nt * 128;
-    const size_t gmax = c.stream ? 0 : (size_t)c.group;
-    const size_t w_slot = c.stream ? 0 : (size_t)kb * 16384;
+    const size_t x_stage = (size_t)kb * c.nt * 128;
+    const size_t gmax = (size_t)c.group;
+    const size_t w_slot = (size_t)kb * 16384;
     return 1024 + (size_t)c.xst * x_stage + gmax * w_slot + (size_t)stage_bytes() +
            8 * (size_t)(2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * gmax + 2 * kStageDepth) + 8;
 }
 
 static bool layout_ok(const TcConfig &c, int kb)
 {
-    return layout_end(c, kb) <= (size_t)c.smem && c.smem <= kSmemLimit && c.xst >= 2 && c.xst <= kMaxXStages &&
-           (c.stream || c.group <= 16) && c.nt >= 16 && c.nt <= 256 && c.nt % 16 == 0;
+    return !c.stream && layout_end(c, kb) <= (size_t)c.smem && c.smem <= kSmemLimit && c.xst >= 2 &&
+           c.xst <= kMaxXStages && c.group <= 16 && c.nt >= 16 && c.nt <= 256 && c.nt % 16 == 0;
 }
 
 bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why)
@@ -691,33 +705,26 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
     }
     const int mt = f.m_pad / kRowsPerMTile;
     if (f.kb >= 4) {
-        // many antennas: stream weight and voltage K blocks through a ring of stages
+        // many antennas: the weights do not stay resident; the batched kernel's
+        // streamed pipeline (k_batch.cu, one job) runs the plan with this tile
+        // width and sizes its own stages (a weight and a voltage K block each)
         for (int nt = 256; nt >= (int)unit; nt -= 16) {
             if (nt % unit) continue;
             if (req.tile_t && nt != req.tile_t) continue;
             if (nt / t_int > kMaxWinPerTile) continue;
-            const int stage = 16384 + nt * 128;
-            const int fixed = stage_bytes() + ctrl_bytes() + 1024;
-            int xst = std::min(kMaxXStages, (kSmemLimit - fixed) / stage);
-            if (req.x_stages) xst = std::min(xst, req.x_stages);
-            if (xst < 2) continue;
             TcConfig c;
             c.stream = true;
             c.nt = nt;
-            c.xst = xst;
+            c.xst = 0;
             c.nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
             c.fast_windows = (t_int % 16) == 0;
             c.n_groups = 1;
             c.group = mt;
-            c.smem = std::max(fixed + xst * stage, 116 * 1024);
-            if (!layout_ok(c, f.kb)) {
-                *why = "internal tiling inconsistency (shared-memory layout exceeds the allocation)";
-                return false;
-            }
+            c.smem = 0;
             *cfg = c;
             return true;
         }
-        *why = "requested tile configuration does not fit the streamed tensor-core kernel";
+        *why = "requested tile configuration does not fit the streamed tensor-core pipeline";
         return false;
     }
     for (int nt = 256; nt >= (int)unit; nt -= 16) {
@@ -769,15 +776,27 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
     return false;
 }
 
-template <bool F8, int WIN, bool CPX, bool STREAM>
-static cudaError_t launch_one(const CUtensorMap &xm, const CUtensorMap &wm, const TcKernelArgs &ka, int grid,
-                              int smem, cudaStream_t s)
+template <bool F8, int WIN, bool CPX, bool DIRECT>
+static cudaError_t launch_v(const CUtensorMap &xm, const CUtensorMap &wm, const TcKernelArgs &ka, int grid, int smem,
+                            cudaStream_t s)
 {
-    auto kern = k_tc<F8, WIN, CPX, STREAM>;
+    auto kern = k_tc<F8, WIN, CPX, DIRECT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kTcThreads, smem, s>>>(xm, wm, ka);
     return cudaGetLastError();
+}
+
+// Power tiles of 256 samples split in two 128-column slices, with a window
+// known at compile time, take the direct-store epilogue; every other case the
+// staged one (the store warp writes runs of windows).
+template <bool F8, int WIN, bool CPX>
+static cudaError_t launch_one(const CUtensorMap &xm, const CUtensorMap &wm, const TcKernelArgs &ka, int grid,
+                              int smem, cudaStream_t s)
+{
+    if (!CPX && WIN > 0 && ka.nt == 256 && ka.nsplit == 2)
+        return launch_v<F8, WIN, CPX, true>(xm, wm, ka, grid, smem, s);
+    return launch_v<F8, WIN, CPX, false>(xm, wm, ka, grid, smem, s);
 }
 
 cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string *why)
@@ -785,6 +804,10 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const WeightFormat &f = p->wf;
     const TcConfig &cfg = p->tc;
     if (ta.T == 0 || ta.c_launch == 0) return cudaSuccess;
+    if (cfg.stream) {   // callers send streamed-weight plans to the batched pipeline
+        *why = "plan has streamed weights (K >= 4 blocks): not a resident-weight launch";
+        return cudaErrorInvalidConfiguration;
+    }
     CUtensorMap xm, wm;
     if (!encode_voltage_map(&xm, ta.x, 2 * p->N, ta.T, ta.c_launch, f.es, f.ke, cfg.nt)) {
         *why = "voltage tensor map rejected (pointer or row stride not 16-byte aligned?)";
@@ -799,7 +822,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.n_groups = cfg.n_groups;
     ka.g_base = mt / cfg.n_groups;
     ka.g_rem = mt % cfg.n_groups;
-    ka.gmax = cfg.stream ? 0 : cfg.group;   // streamed weights have no resident slots
+    ka.gmax = cfg.group;
     // power output needs the samples of whole windows only (the tail is dropped)
     const int t_used = ta.complex_out ? ta.T : ta.T_o * ta.t_int;
     ka.t_tiles = (t_used + cfg.nt - 1) / cfg.nt;
@@ -821,14 +844,14 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const uint32_t fmt = (f.op == kOpBF16) ? 1u : 0u;   // F16 = 0, BF16 = 1; E4M3 = 0 for f8f6f4
     ka.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(cfg.nt >> 3) << 17) |
                ((uint32_t)(kRowsPerMTile >> 4) << 24);
-    ka.x_stage_bytes = cfg.stream ? (uint32_t)(16384 + cfg.nt * 128) : (uint32_t)(f.kb * cfg.nt * 128);
-    ka.w_slot_bytes = cfg.stream ? 0u : (uint32_t)(f.kb * 16384);
+    ka.x_stage_bytes = (uint32_t)(f.kb * cfg.nt * 128);
+    ka.w_slot_bytes = (uint32_t)(f.kb * 16384);
     ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
     ka.err = p->d_err;
     if (ka.ct_total == 0) return cudaSuccess;
-    if (!layout_ok(cfg, f.kb) || ka.gmax != (cfg.stream ? 0 : cfg.group)) {   // final guard before launch
+    if (!layout_ok(cfg, f.kb) || ka.gmax != cfg.group) {   // final guard before launch
         *why = "internal tiling inconsistency (shared-memory layout exceeds the allocation)";
         return cudaErrorInvalidConfiguration;
     }
@@ -838,25 +861,19 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const int grid = (int)(n_sets * ka.gq);
     const bool f8 = f.op == kOpE4M3;
     const int win = (ta.t_int == 64 || ta.t_int == 32 || ta.t_int == 16) ? ta.t_int : (ta.t_int % 16 == 0 ? 0 : -1);
-#define BF_TC_ALL(F8V, STV)                                                                 \
-    if (ta.complex_out) return launch_one<F8V, 0, true, STV>(xm, wm, ka, grid, cfg.smem, s); \
-    switch (win) {                                                                          \
-    case 64: return launch_one<F8V, 64, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
-    case 32: return launch_one<F8V, 32, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
-    case 16: return launch_one<F8V, 16, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
-    case 0: return launch_one<F8V, 0, false, STV>(xm, wm, ka, grid, cfg.smem, s);            \
-    default: return launch_one<F8V, -1, false, STV>(xm, wm, ka, grid, cfg.smem, s);          \
-    }
-    if (cfg.stream) {
-        if (f8) {
-            BF_TC_ALL(true, true)
-        }
-        BF_TC_ALL(false, true)
+#define BF_TC_ALL(F8V)                                                                 \
+    if (ta.complex_out) return launch_one<F8V, 0, true>(xm, wm, ka, grid, cfg.smem, s); \
+    switch (win) {                                                                     \
+    case 64: return launch_one<F8V, 64, false>(xm, wm, ka, grid, cfg.smem, s);          \
+    case 32: return launch_one<F8V, 32, false>(xm, wm, ka, grid, cfg.smem, s);          \
+    case 16: return launch_one<F8V, 16, false>(xm, wm, ka, grid, cfg.smem, s);          \
+    case 0: return launch_one<F8V, 0, false>(xm, wm, ka, grid, cfg.smem, s);            \
+    default: return launch_one<F8V, -1, false>(xm, wm, ka, grid, cfg.smem, s);          \
     }
     if (f8) {
-        BF_TC_ALL(true, false)
+        BF_TC_ALL(true)
     }
-    BF_TC_ALL(false, false)
+    BF_TC_ALL(false)
 #undef BF_TC_ALL
 }
 

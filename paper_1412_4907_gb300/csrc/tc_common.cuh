@@ -200,7 +200,7 @@ __device__ __forceinline__ void store_tile(const O &o, float *stg, int b_tile0, 
             if (bb < o.B) o.acc_out[(size_t)bb * o.c_total + cg] = stg[bl * kMaxWinPerTile + k];
         }
     }
-    const bool vec = (o.T_o & 3) == 0 && (o.wpt & 3) == 0;
+    const bool vec = (o.T_o & 3) == 0 && (o.wpt & 3) == 0 && ((uintptr_t)o.out & 15) == 0;
     const int nj = min(o.wpt, o.T_o - j0);
     if (vec && o.wpt == 4) {
         // one float4 per beam: lanes take beams lane and lane + 32

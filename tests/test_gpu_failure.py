@@ -38,5 +38,5 @@ def test_bounded_wait_reports_timeout_and_context_survives(bf):
     P = plan.execute(torch.from_numpy(np.ascontiguousarray(x)).cuda())
     plan.sync()
     mx, l2 = rel_errors(P.cpu().numpy(), oracle_power_for_mode(scene, dirs, 64, synth.C16F, X64))
-    assert mx <= 1e-4 and l2 <= 1e-5
+    assert mx <= 2e-5 and l2 <= 5e-6   # the tensor-core tolerance of test_gpu_parity
     plan.close()

@@ -5,8 +5,9 @@ those outputs).
 
 - Batched: the 48 sub-array jobs (74 GB of FP16 voltages made on the device
   by the bench's seeded generator) in one graph-captured launch with the
-  bench's autotuned tile width; sampled (job, channel, beam) outputs against
-  the oracle fed the same FP16 values and weights.
+  bench's autotuned tile width; every job is sampled (one channel, 16 beams,
+  the first and the last 8 windows) against the oracle fed the same FP16
+  values and weights.
 - Serving: the six stream configurations at full size, two chunks per stream
   (the second continues the first's open window); sampled beams of one
   channel per stream against the oracle on the concatenated samples.
@@ -22,7 +23,7 @@ from helpers import rel_errors
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-TOL = {synth.C16F: (1e-4, 1e-5), synth.CI8: (1e-4, 1e-5)}
+TOL = {synth.C16F: (2e-5, 5e-6), synth.CI8: (2e-5, 5e-6)}   # as in test_gpu_parity
 
 
 @pytest.fixture(scope="module")
@@ -56,16 +57,19 @@ def test_batched_jobs_full_size_sampled(bf):
     batch.replay()
     batch.sync()
     g = np.random.default_rng(44)
-    for j in g.choice(len(jobs), size=6, replace=False):
-        job, p = jobs[j], plans[j]
+    for j, (job, p) in enumerate(zip(jobs, plans)):
         c = int(g.integers(0, p.C))
-        beams = np.sort(g.choice(p.B, size=min(p.B, 48), replace=False))
-        X64 = oracle.decode_voltages(synth.C16F, xs[j][c:c + 1, :1024].cpu().numpy())   # first 16 windows
+        beams = np.sort(g.choice(p.B, size=min(p.B, 16), replace=False))
         W = oracle.quantised_weights(oracle.weights(job.scene.pos, job.scene.freqs[c:c + 1], job.dirs[beams]),
                                      synth.C16F)[0]
-        P_ref = oracle.power(W, X64, job.t_int)
-        P = outs[j][torch.from_numpy(beams).cuda(), c:c + 1, :16].cpu().numpy()
-        check(f"job{j}_c{c}", P, P_ref, synth.C16F)
+        n_win = job.scene.n_samp // job.t_int
+        bsel = torch.from_numpy(beams).cuda()
+        for w0 in (0, n_win - 8):   # the first and the last 8 windows
+            t0 = w0 * job.t_int
+            X64 = oracle.decode_voltages(synth.C16F, xs[j][c:c + 1, t0:t0 + 8 * job.t_int].cpu().numpy())
+            P_ref = oracle.power(W, X64, job.t_int)
+            P = outs[j][bsel, c:c + 1, w0:w0 + 8].cpu().numpy()
+            check(f"job{j}_c{c}_w{w0}", P, P_ref, synth.C16F)
     batch.close()
     for p in plans:
         p.close()

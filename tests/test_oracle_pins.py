@@ -265,8 +265,11 @@ def test_p8_paper_arithmetic():
     bits = r["channels"] * r["samples_per_s"] * r["antennas"] * r["bits_per_word"]
     assert bits / 1e9 == pytest.approx(r["gbps"], rel=1e-12)
     k = g["k20_flops"]
-    # the paper rounds both numbers ("~1.3", "approximately 38%"): 1.3/3.52 = 36.9%
-    assert k["tflops"] / k["k20_peak_tflops"] == pytest.approx(k["fraction_of_peak"], abs=0.015)
+    # the paper rounds both numbers ("~1.3", "approximately 38%"); the peak they
+    # imply, 1.3 / 0.38 = 3.42 TFLOP/s, agrees with the vendor's 3.52 (an outside
+    # figure, not the paper's) within that rounding
+    implied_peak = k["tflops"] / k["fraction_of_peak"]
+    assert implied_peak == pytest.approx(g["outside_the_paper"]["k20_peak_tflops"], rel=0.04)
     t = g["table3"]
     stages = (t["beamforming_ms"] + t["bandpass_ms"] + t["rfi_ms"] + t["dedispersion_ms"]
               + t["median_ms"] + t["detrend_ms"])
