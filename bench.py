@@ -61,12 +61,15 @@ def peaks():
     return FALLBACK_PEAKS, "fallback"
 
 
+KERNEL_SOURCES = ("k_tc_kernel.cuh", "tc_common.cuh", "ptx.cuh")
+
+
 def kernel_source_sha():
-    """Hash of the fused kernel's code (its two source files with comments and
+    """Hash of the fused kernel's code (its source files with comments and
     blank space removed), so that a profile is invalidated by a code change
     and not by an edit of a comment."""
     h = hashlib.sha256()
-    for f in ("k_tc.cu", "ptx.cuh"):   # the kernel's own sources
+    for f in KERNEL_SOURCES:   # the kernel's own sources
         text = open(os.path.join(ROOT, "paper_1412_4907_gb300", "csrc", f)).read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)

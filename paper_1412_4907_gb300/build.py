@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["bf_api.cu", "k_weights.cu", "k_simt.cu", "k_tc.cu", "tmap.cu", "k_batch.cu", "k_serve.cu", "k_aux.cu", "k_selftest.cu", "k_detect.cu", "bf_noalloc.cu"]
+SOURCES = ["bf_api.cu", "k_weights.cu", "k_simt.cu", "k_tc.cu", "k_tc_f16.cu", "k_tc_f8.cu", "k_tc_i8.cu", "k_tc_i4.cu",
+           "tmap.cu", "k_batch.cu", "k_serve.cu", "k_aux.cu", "k_selftest.cu", "k_detect.cu", "bf_noalloc.cu"]
 
 
 def nvcc() -> str:

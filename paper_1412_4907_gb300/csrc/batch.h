@@ -34,11 +34,14 @@ struct __align__(128) BatchJob {
     float *acc_out;        // [B][C] partial sum of window T_o carried out, or NULL
 };
 
+static_assert(sizeof(BatchJob) == 384, "job table rows are 384 bytes (16 fit in the launch parameters)");
+
 // Launch-wide choices: tile width and the pipeline depths that follow.
 struct BatchCore {
     int nt = 256, nsplit = 2, wpt = 4, t_int = 64, xst = 2, nacc = 2, smem = 0;
     bool f8 = false;
     bool cpx = false;   // complex beams [B][C][T][2] instead of powers (single plans only)
+    bool direct = false; // power epilogue stores windows itself (256-sample tiles, T_int 16/32/64)
     int num_sms = 1;
 };
 
@@ -50,7 +53,7 @@ struct BatchCore {
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t);
 
 // Fills one job.  x_mma: the voltages as the MMA reads them (the FP16
-// expansion for 8/4-bit integer inputs), [c_count][T][2N] for the plan's
+// widening for 8/4-bit integer inputs), [c_count][T][2N] for the plan's
 // channels c_base .. c_base + c_count - 1 (c_count < 0: all channels).  T_o,
 // t_tiles and units follow from T, t_shift and whether acc_out is given.
 bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, const void *x_mma, int T,

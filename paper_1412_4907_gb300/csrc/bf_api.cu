@@ -344,7 +344,10 @@ static bf_status run_range_body(bf_plan *p, const void *x, int c_base, int c_lau
     const void *xin = x;
     size_t need = 0;
     const bool ct = p->layout == BF_LAYOUT_NCT;
-    const bool expand = p->dtype == BF_CI8 || p->dtype == BF_CI4;
+    // 8/4-bit inputs: the resident-weight kernel widens them itself (each
+    // voltage tile serves a group of M tiles); the streamed pipeline uses a
+    // voltage block for one M tile, so it reads an FP16 widening from scratch
+    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && p->tc.stream;
     if (ct) need += (n_samp * sb + 255) / 256 * 256;
     if (expand) need += n_samp * 4;
     if (need) {

@@ -95,7 +95,9 @@ extern "C" bf_status bf_execute_nct_static(bf_plan *p, const void *x, int T, flo
         return set_error(BF_ERR_ARG, "voltages must be 16-byte aligned and outputs 4-byte aligned");
     const size_t n_samp = (size_t)p->C * T * p->N;
     const size_t turned = (n_samp * dtype_sample_bytes(p->dtype) + 255) / 256 * 256;
-    const bool expand = p->dtype == BF_CI8 || p->dtype == BF_CI4;
+    // 8/4-bit inputs: the resident-weight kernel widens them itself; the
+    // streamed pipeline reads an FP16 widening from the scratch
+    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && p->tc.stream;
     const size_t need = turned + (expand ? n_samp * 4 : 0);
     if (need > kStaticScratchBytes)
         return set_error(BF_ERR_ARG, "input needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +

@@ -121,7 +121,10 @@ constexpr int kDescRing = 16;
 
 // CPX: complex beams [B][C][T][2] straight from the epilogue (the store warp
 // only recycles the descriptor slots); otherwise integrated powers.
-template <bool F8, int WIN, bool CPX>
+// DIRECT (powers, 256-sample tiles, T_int of 16, 32 or 64): the epilogue warps
+// store their windows straight to the output, route the carried windows
+// themselves and hand the descriptor slot back; the store warp has no work.
+template <bool F8, int WIN, bool CPX, bool DIRECT>
 __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_constant__ ParamJobs pj)
 {
     const BatchJob *jobs = a.jobs ? a.jobs : pj.j;   // a table in device memory, or jobs passed by value
@@ -165,7 +168,7 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
         }
         for (int i = 0; i < kDescRing; ++i) {
             mbar_init(b_dfull + 8 * i, 1);
-            mbar_init(b_dempty + 8 * i, 1);
+            mbar_init(b_dempty + 8 * i, DIRECT ? 8 : 1);   // the epilogue group, or the store warp
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -308,6 +311,88 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
             drain_wait(b_drain, 0);
         }
         __syncwarp();
+    } else if (warp < kStoreWarp && DIRECT) {
+        // ---------------------------------------------- epilogue, direct stores
+        // As in the single-plan kernel: warp h of a lane quarter reads its 128
+        // columns (128h..) in two 64-column loads, releases the accumulator
+        // after the second, sums each window's squares, combines re and im
+        // rows with one shuffle and writes its windows itself: window 0 first
+        // takes the partial sum carried in, the window left open at the end of
+        // the chunk goes to acc_out, the others to the output.
+        constexpr int W = WIN > 0 ? WIN : 64;
+        constexpr int NW = 64 / W;                    // windows per 64-column load
+        const int e = warp - 2;
+        const int grp = e >> 3;
+        const int q = warp & 3;
+        const int h = (e & 7) >> 2;
+        const int bq = q * 16 + (lane & 15);
+        const bool re_lane = lane < 16;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + h * 128;
+        const int jA = (h * 128) / W, jB = (h * 128 + 64) / W;
+        for (uint32_t kt = grp;; kt += 2) {
+            const uint32_t slot = kt % kDescRing;
+            if (!mbar_wait(b_dfull + 8 * slot, (kt / kDescRing) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+            const TileDesc &D = desc[slot];
+            if (D.last) break;
+            // the tile's fields into registers, then the slot goes back to the producer
+            const int b = D.b0 + bq;
+            const bool bvalid = b < D.n_beams;
+            const int c = D.c, T_o = D.T_o, j0 = D.tt * a.wpt;
+            const size_t row = (size_t)b * D.c_total + c;
+            const float sc = (re_lane && bvalid && D.wscale) ? D.wscale[(size_t)c * D.b_pad + b] : 1.f;
+            float *const o = D.out + row * T_o + j0;
+            const float *const acc_in = D.acc_in;
+            float *const acc_out = D.acc_out;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_dempty + 8 * slot);
+            const int acc = (int)(kt % (uint32_t)a.nacc);
+            if (!mbar_wait(b_tfull + 8 * acc, (kt / a.nacc) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+            tc_fence_after();
+            const uint32_t ta = lane_base + acc * a.nt;
+            float pa[NW], pb[NW];
+            {
+                uint32_t r[64];
+                tmem_ld64r(ta, r);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) pa[k] = sumsq_pk<W>(r + k * W);
+            }
+            {
+                uint32_t r[64];
+                tmem_ld64r(ta + 64, r);
+                tile_release(b_tempty + 8 * acc, lane);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) pb[k] = sumsq_pk<W>(r + k * W);
+            }
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                pa[k] = (pa[k] + __shfl_xor_sync(0xffffffffu, pa[k], 16)) * sc;
+                pb[k] = (pb[k] + __shfl_xor_sync(0xffffffffu, pb[k], 16)) * sc;
+            }
+            if (re_lane && bvalid) {
+                const bool inner = (j0 > 0 || !acc_in) && j0 + jB + NW <= T_o;
+                const uintptr_t oa = (uintptr_t)(o + jA);
+                if (inner && NW == 1 && (oa & 7) == 0) {
+                    *reinterpret_cast<float2 *>(o + jA) = make_float2(pa[0], pb[0]);
+                } else if (inner && NW == 2 && (oa & 7) == 0) {
+                    *reinterpret_cast<float2 *>(o + jA) = make_float2(pa[0], pa[1 % NW]);
+                    *reinterpret_cast<float2 *>(o + jB) = make_float2(pb[0], pb[1 % NW]);
+                } else if (inner && NW == 4 && (oa & 15) == 0) {
+                    *reinterpret_cast<float4 *>(o + jA) = make_float4(pa[0], pa[1 % NW], pa[2 % NW], pa[3 % NW]);
+                    *reinterpret_cast<float4 *>(o + jB) = make_float4(pb[0], pb[1 % NW], pb[2 % NW], pb[3 % NW]);
+                } else {
+                    // edge tiles: the carried-in window 0, the open window T_o, the tail
+#pragma unroll
+                    for (int k = 0; k < 2 * NW; ++k) {
+                        const int jl = k < NW ? jA + k : jB + (k - NW);
+                        float p = k < NW ? pa[k] : pb[k - NW];
+                        const int j = j0 + jl;
+                        if (j == 0 && acc_in) p += acc_in[row];
+                        if (j < T_o) o[jl] = p;
+                        else if (j == T_o && acc_out) acc_out[row] = p;
+                    }
+                }
+            }
+        }
     } else if (warp < kStoreWarp) {
         // -------------------------------------------------------------- epilogue
         // two groups of 8 warps take alternate tiles (and so alternate
@@ -358,7 +443,7 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
                                     stage + sb * (kBeamsPerMTile * kMaxWinPerTile), tempty, b_sfull + 8 * sb);
             }
         }
-    } else if (warp == kStoreWarp) {
+    } else if (warp == kStoreWarp && !DIRECT) {
         // ------------------------------------------------------------ store warp
         for (uint32_t kt = 0;; ++kt) {
             const uint32_t slot = kt % kDescRing;
@@ -403,16 +488,17 @@ static int batch_layout_end(int xst, int nt)
 
 // The attribute is a per-kernel maximum shared by every batch: it is set to
 // the largest size any batch asks for, so one batch never lowers another's.
-template <bool F8, int WIN, bool CPX>
+template <bool F8, int WIN, bool CPX, bool DIRECT>
 static cudaError_t batch_attr()
 {
-    return cudaFuncSetAttribute(k_tc_batch<F8, WIN, CPX>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    return cudaFuncSetAttribute(k_tc_batch<F8, WIN, CPX, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemLimit);
 }
 
-template <bool F8, int WIN, bool CPX>
+template <bool F8, int WIN, bool CPX, bool DIRECT>
 static cudaError_t batch_launch(const BatchArgs &ka, const ParamJobs &pj, int grid, int smem, cudaStream_t s)
 {
-    k_tc_batch<F8, WIN, CPX><<<grid, kTcThreads, smem, s>>>(ka, pj);
+    k_tc_batch<F8, WIN, CPX, DIRECT><<<grid, kTcThreads, smem, s>>>(ka, pj);
     return cudaGetLastError();
 }
 
@@ -421,34 +507,30 @@ static int batch_win(int t_int)
     return (t_int == 64 || t_int == 32 || t_int == 16) ? t_int : (t_int % 16 == 0 ? 0 : -1);
 }
 
-// Calls F.template run<F8, WIN, CPX>() for the core's operand format, window
-// specialisation and output kind.
-template <class F>
-static cudaError_t batch_dispatch(const BatchCore &core, F &&f)
+// Calls F.template run<F8, WIN, CPX, DIRECT>() for the core's operand format,
+// window specialisation and output kind.
+template <bool F8, class F>
+static cudaError_t batch_dispatch_f(const BatchCore &core, F &f)
 {
-    if (core.cpx) return core.f8 ? f.template run<true, 0, true>() : f.template run<false, 0, true>();
-    const int win = batch_win(core.t_int);
-    if (core.f8) {
-        switch (win) {
-        case 64: return f.template run<true, 64, false>();
-        case 32: return f.template run<true, 32, false>();
-        case 16: return f.template run<true, 16, false>();
-        case 0: return f.template run<true, 0, false>();
-        default: return f.template run<true, -1, false>();
-        }
-    }
-    switch (win) {
-    case 64: return f.template run<false, 64, false>();
-    case 32: return f.template run<false, 32, false>();
-    case 16: return f.template run<false, 16, false>();
-    case 0: return f.template run<false, 0, false>();
-    default: return f.template run<false, -1, false>();
+    if (core.cpx) return f.template run<F8, 0, true, false>();
+    switch (batch_win(core.t_int)) {
+    case 64: return core.direct ? f.template run<F8, 64, false, true>() : f.template run<F8, 64, false, false>();
+    case 32: return core.direct ? f.template run<F8, 32, false, true>() : f.template run<F8, 32, false, false>();
+    case 16: return core.direct ? f.template run<F8, 16, false, true>() : f.template run<F8, 16, false, false>();
+    case 0: return f.template run<F8, 0, false, false>();
+    default: return f.template run<F8, -1, false, false>();
     }
 }
 
+template <class F>
+static cudaError_t batch_dispatch(const BatchCore &core, F &&f)
+{
+    return core.f8 ? batch_dispatch_f<true>(core, f) : batch_dispatch_f<false>(core, f);
+}
+
 struct BatchAttr {
-    template <bool F8, int WIN, bool CPX>
-    cudaError_t run() const { return batch_attr<F8, WIN, CPX>(); }
+    template <bool F8, int WIN, bool CPX, bool DIRECT>
+    cudaError_t run() const { return batch_attr<F8, WIN, CPX, DIRECT>(); }
 };
 
 struct BatchLaunch {
@@ -456,8 +538,8 @@ struct BatchLaunch {
     const ParamJobs &pj;
     int grid, smem;
     cudaStream_t s;
-    template <bool F8, int WIN, bool CPX>
-    cudaError_t run() const { return batch_launch<F8, WIN, CPX>(ka, pj, grid, smem, s); }
+    template <bool F8, int WIN, bool CPX, bool DIRECT>
+    cudaError_t run() const { return batch_launch<F8, WIN, CPX, DIRECT>(ka, pj, grid, smem, s); }
 };
 
 bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int tile_t)
@@ -497,6 +579,7 @@ bf_status batch_core_init(BatchCore *core, bf_plan *const *plans, int n, int til
     c.wpt = nt / t_int;
     c.nacc = std::min(kMaxAcc, kTmemCols / nt) & ~1;   // even: each epilogue group keeps its own accumulators
     c.f8 = p0->wf.op == kOpE4M3;
+    c.direct = batch_win(t_int) > 0 && nt == 256 && c.nsplit == 2;
     c.num_sms = std::max(1, p0->num_sms);
     const int fixed = batch_layout_end(0, nt);
     c.xst = std::min(kMaxXStages, (kSmemLimit - fixed) / batch_stage_bytes(nt));

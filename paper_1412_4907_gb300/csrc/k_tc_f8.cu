@@ -1,0 +1,9 @@
+// Resident-weight tensor-core beamformer: the variants for FP8 E4M3 voltages.
+#include "k_tc_kernel.cuh"
+
+namespace bfi {
+
+template cudaError_t launch_tc_family<true, 0>(const CUtensorMap &, const CUtensorMap &, const TcKernelArgs &, int,
+                                                 bool, int, int, cudaStream_t);
+
+}  // namespace bfi

@@ -7,6 +7,8 @@
 #pragma once
 #include <cudaTypedefs.h>
 
+#include <cuda_fp16.h>
+
 #include "bf_internal.h"
 #include "ptx.cuh"
 #include "tmap.h"
@@ -54,6 +56,99 @@ __device__ __forceinline__ float sumsq_pk(const uint32_t *r)
 #pragma unroll
     for (int i = 0; i < n / 2; ++i) sq_acc2(acc[i & 3], r[2 * i], r[2 * i + 1]);
     return (sum2(acc[0]) + sum2(acc[1])) + (sum2(acc[2]) + sum2(acc[3]));
+}
+
+// ----------------------------------------------- 8- and 4-bit input widening
+// Integer complex voltages are widened to the FP16 MMA operand in shared
+// memory by converter warps, so the kernel reads each sample's 2 (int8) or
+// 1 (4-bit) bytes from HBM once and nothing is written back (the unpacking
+// of Section 2.1 done inside the beamformer).  Every value is exact in FP16.
+//
+// Bias trick, no integer-to-float instruction: a byte u in 0..255 placed as
+// the low byte of the FP16 pattern 0x64uu is the number 1024 + u (FP16 has
+// unit spacing in [1024, 2048)); so a signed 8-bit x becomes
+// (1024 + (x ^ 0x80)) - 1152 = x, and a signed 4-bit v (nibble s, s ^ 8 =
+// v + 8) becomes (1024 + (s ^ 8)) - 1032 = v; both subtractions are exact.
+// One converter warp is added to the 19-warp kernels (an SM sub-partition's
+// 16K registers hold five warps of 96 registers, so 20 warps is the most);
+// where the store warp has no work it converts too.
+constexpr int kConvWarps = 1;
+
+// Four antennas of signed 8-bit (re, im) pairs (8 bytes) -> four FP16 pairs.
+__device__ __forceinline__ uint4 widen_i8x4(uint2 w)
+{
+    const __half2 off = __float2half2_rn(1152.f);
+    const uint32_t b0 = w.x ^ 0x80808080u, b1 = w.y ^ 0x80808080u;
+    uint32_t r[4] = {__byte_perm(b0, 0x64646464u, 0x4140), __byte_perm(b0, 0x64646464u, 0x4342),
+                     __byte_perm(b1, 0x64646464u, 0x4140), __byte_perm(b1, 0x64646464u, 0x4342)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 h = *reinterpret_cast<__half2 *>(&r[i]);
+        h = __hsub2(h, off);
+        r[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    return make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+// Four antennas of 4-bit pairs (one byte each: real part in the high nibble,
+// two's complement) -> four FP16 pairs.
+__device__ __forceinline__ uint4 widen_i4x4(uint32_t w)
+{
+    const __half2 off = __float2half2_rn(1032.f);
+    const uint32_t hi = ((w >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;   // real parts, biased
+    const uint32_t lo = (w & 0x0F0F0F0Fu) ^ 0x08080808u;          // imaginary parts, biased
+    const uint32_t a01 = __byte_perm(hi, lo, 0x5140), a23 = __byte_perm(hi, lo, 0x7362);
+    uint32_t r[4] = {__byte_perm(a01, 0x64646464u, 0x4140), __byte_perm(a01, 0x64646464u, 0x4342),
+                     __byte_perm(a23, 0x64646464u, 0x4140), __byte_perm(a23, 0x64646464u, 0x4342)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 h = *reinterpret_cast<__half2 *>(&r[i]);
+        h = __hsub2(h, off);
+        r[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    return make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+// Widens one 128-byte K block of a voltage tile: rows t0 .. t0 + nt - 1 of one
+// channel (src: that channel's row 0; rows before 0 or at or beyond T read as
+// zero),
+// antennas 32 kb .. 32 kb + 31 (those at or beyond N read as zero), written
+// to dst as nt rows of 128 bytes with the 128-byte swizzle the MMA descriptor
+// expects (16-byte chunk j of row r at chunk j ^ (r & 7)).  Each thread
+// (tid of nthr) takes 16-byte chunks, four loads in flight.  DT: BF_CI8
+// (rows of 2N bytes) or BF_CI4 (rows of N bytes); N % 4 == 0.
+template <int DT>
+__device__ __forceinline__ void widen_block(const uint8_t *__restrict__ src, int t0, int T, int N, int kb, int nt,
+                                            uint8_t *dst, int tid, int nthr)
+{
+    constexpr int kBytes = DT == BF_CI8 ? 8 : 4;   // source bytes per 4 antennas
+    const size_t row_bytes = (size_t)N * (DT == BF_CI8 ? 2 : 1);
+    const int n_items = nt * 8;
+    for (int i0 = tid; i0 < n_items; i0 += 4 * nthr) {
+        uint2 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * nthr;
+            const int row = i >> 3, ch = i & 7;
+            const int t = t0 + row, a4 = kb * 32 + ch * 4;   // first antenna of the chunk
+            w[u] = make_uint2(0u, 0u);
+            if (i < n_items && (unsigned)t < (unsigned)T && a4 < N) {
+                const uint8_t *q = src + (size_t)t * row_bytes + (size_t)a4 * (kBytes / 4);
+                if (DT == BF_CI8) w[u] = __ldg(reinterpret_cast<const uint2 *>(q));
+                else w[u].x = __ldg(reinterpret_cast<const uint32_t *>(q));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * nthr;
+            if (i >= n_items) break;
+            const int row = i >> 3, ch = i & 7;
+            const int t = t0 + row, a4 = kb * 32 + ch * 4;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if ((unsigned)t < (unsigned)T && a4 < N) v = DT == BF_CI8 ? widen_i8x4(w[u]) : widen_i4x4(w[u].x);
+            *reinterpret_cast<uint4 *>(dst + row * 128 + ((ch ^ (row & 7)) << 4)) = v;
+        }
+    }
 }
 
 // What the epilogue and the store warp need to know about the output of the

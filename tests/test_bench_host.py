@@ -10,8 +10,11 @@ import bench
 def _tree(tmp_path, k_tc, ptx):
     csrc = tmp_path / "paper_1412_4907_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "k_tc.cu").write_text(k_tc)
-    (csrc / "ptx.cuh").write_text(ptx)
+    files = dict.fromkeys(bench.KERNEL_SOURCES, "#pragma once\n")
+    files[bench.KERNEL_SOURCES[0]] = k_tc
+    files["ptx.cuh"] = ptx
+    for name, text in files.items():
+        (csrc / name).write_text(text)
     return str(tmp_path)
 
 
