@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "beamform TFLOP/s & roofline %, p99 chunk latency: mixed-prec vs FP32, 1 GB300"
+INPUTS = {"c16f": synth.C16F, "ci8": synth.CI8, "ci4": synth.CI4}
+INPUT_SIGMA = {synth.CI8: 16.0, synth.CI4: 2.0}   # noise per component of the integer-input variants
 UNIT = "TFLOP/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 PROFILE = os.path.join(ROOT, "profiles", "k_tc_config2.json")
@@ -227,12 +229,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(scene, dirs, t_int, scaling="weak"):
-    return {"workload": f"real-time FP16 chunk: 32-antenna BEST-2 grid, {scene.n_chan} channels x 15625 "
+def config_dict(scene, dirs, t_int, scaling="weak", mode=synth.C16F):
+    name = {synth.C16F: "FP16", synth.CI8: "8-bit integer", synth.CI4: "4-bit integer"}[mode]
+    vb = scene.n_chan * scene.n_samp * scene.n_ant * synth.MODE_BYTES[mode] / 1e9
+    return {"workload": f"real-time {name} chunk: 32-antenna BEST-2 grid, {scene.n_chan} channels x 15625 "
                         "samples, 1024 beams, T_int 64",
             "n_ant": scene.n_ant, "n_chan": scene.n_chan, "n_beam": int(dirs.shape[0]),
-            "n_samp": scene.n_samp, "t_int": t_int, "input": "c16f, [c][t][n] (no corner turn)",
-            "l2": "no flush: voltages (2.05 GB) and weights (0.27 GB) exceed the 129 MB L2",
+            "n_samp": scene.n_samp, "t_int": t_int,
+            "input": f"{synth.MODE_NAMES[mode]}, [c][t][n] (no corner turn)"
+                     + ("" if mode == synth.C16F else "; widened to FP16 inside the beamformer"),
+            "l2": f"no flush: voltages ({vb:.2f} GB) and weights (0.27 GB) exceed the 129 MB L2",
             "parallelism": ("channels: one independent chunk per GPU, no collective" if scaling == "weak" else
                             "channels: contiguous channel ranges of one chunk per GPU, no collective")}
 
@@ -249,7 +255,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    scene, dirs, t_int = synth.config2()
+    mode = INPUTS[args.input]
+    scene, dirs, t_int = synth.config2(INPUT_SIGMA.get(mode))
     if args.channels:   # a band subset with the same per-channel shape (profiling captures)
         scene.freqs = scene.freqs[:args.channels]
     C_job = scene.n_chan
@@ -259,10 +266,10 @@ def run_ours(args):
     N, C, B, T = scene.n_ant, scene.n_chan, dirs.shape[0], scene.n_samp
     T_o = T // t_int
     F = flops(N, B, C, T)
-    x_host = synth.voltages(scene, synth.C16F)
+    x_host = synth.voltages(scene, mode)
     xd = torch.from_numpy(x_host).cuda()
     stream = torch.cuda.current_stream()
-    plan = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C16F, t_int, stream=stream)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, mode, t_int, stream=stream)
     plan.set_weight_buffers(2)   # the refresh for chunk i+1 overlaps the beamforming of chunk i
     out = torch.empty((B, C, T_o), dtype=torch.float32, device="cuda")
     dirs_alt = [dirs, synth.beam_grid(32, 32, 9.99)]   # re-pointed every chunk
@@ -368,7 +375,8 @@ def run_ours(args):
     hbm = pk["hbm_gbs"]
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "frac_burst": achieved / burst, "frac_sustained": achieved / sust,
-            "traffic": profiled_traffic(), "kernel": "k_tc (fused beamform+detect+integrate)",
+            "traffic": profiled_traffic() if mode == synth.C16F else None,
+            "kernel": "k_tc (fused beamform+detect+integrate)",
             "peak_source": peak_src + " (FP16 = BF16 rate)", "timed_region_ms": total_ms,
             "algorithmic_bytes": alg_bytes + w_bytes,
             "hbm_frac": (alg_bytes + w_bytes) / (k_ms * 1e-3) / 1e9 / hbm}
@@ -384,8 +392,10 @@ def run_ours(args):
                "sample": f"{n_chan} of 1024 channels (all beams, all samples), {dt:.1f} s"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": args.scaling,
-            "vs_baseline": None, "dtype": "f16", "data": "synthetic: seeded complex Gaussian noise + 3 plane waves",
-            "config": config_dict(scene, dirs, t_int, args.scaling), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "vs_baseline": None, "dtype": {synth.C16F: "f16", synth.CI8: "i8", synth.CI4: "i4"}[mode],
+            "data": "synthetic: seeded complex Gaussian noise + 3 plane waves",
+            "config": config_dict(scene, dirs, t_int, args.scaling, mode), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": e2e,
             "gpu_launches": 3 * args.steps * 1,
             "breakdown_ms": {"beamform": k_ms, "weights_alone": w_ms,
                              "weights": "refreshed every chunk on a side stream, overlapped with the beamformer"},
@@ -1020,6 +1030,9 @@ def main():
                     help="second arrival rate of the default run (within the host link's rate)")
     ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched uneven launch")
     ap.add_argument("--no-serve", action="store_true", help="default run: skip the serving runs")
+    ap.add_argument("--input", default="c16f", choices=sorted(INPUTS),
+                    help="sample format of the real-time chunk (default FP16; ci8/ci4: integer samples widened "
+                         "inside the beamformer)")
     ap.add_argument("--channels", type=int, default=0,
                     help="run only the first C channels (same per-channel shape; for profiling)")
     args = ap.parse_args()

@@ -131,7 +131,8 @@ bf_status bf_weights(bf_plan *plan, const double *dirs);
  * normalisation); per-beam weight scales of the FP8/int8 modes are applied.
  * 8- and 4-bit integer samples are widened to FP16 inside the beamforming
  * kernel when the weights stay resident (K <= 3 blocks of 128 bytes per
- * weight row, e.g. up to 96 antennas); plans with streamed weights widen
+ * weight row, e.g. up to 96 antennas) and a sample row is a multiple of 16
+ * bytes (N % 8 == 0 for 8-bit, N % 16 == 0 for 4-bit); other plans widen
  * them into plan scratch first (4 bytes per sample).
  * Errors: BF_ERR_ARG (NULL pointer, n_samp < 0, misaligned pointer).
  */
@@ -478,9 +479,9 @@ bf_status bf_selftest_timeout(double limit_ms, void *stream);
  * the library holds until the process exits.
  *  d_voltages, n_samp, d_power, stream: as bf_execute.  The corner-turned
  *  input, C * n_samp * N samples of the plan's dtype (plus 4 bytes per sample
- *  for BF_CI8 / BF_CI4 plans with streamed weights, K >= 4 blocks: their
- *  FP16 widening), must fit in the 64 MiB; larger inputs return BF_ERR_ARG
- *  without doing anything.
+ *  for BF_CI8 / BF_CI4 plans that bf_execute widens in scratch, see there),
+ *  must fit in the 64 MiB; larger inputs return BF_ERR_ARG without doing
+ *  anything.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the one array and it keeps the last call's

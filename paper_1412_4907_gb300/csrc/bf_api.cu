@@ -345,9 +345,10 @@ static bf_status run_range_body(bf_plan *p, const void *x, int c_base, int c_lau
     size_t need = 0;
     const bool ct = p->layout == BF_LAYOUT_NCT;
     // 8/4-bit inputs: the resident-weight kernel widens them itself (each
-    // voltage tile serves a group of M tiles); the streamed pipeline uses a
-    // voltage block for one M tile, so it reads an FP16 widening from scratch
-    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && p->tc.stream;
+    // voltage tile serves a group of M tiles) when TMA can read their rows;
+    // the streamed pipeline uses a voltage block for one M tile, so it (and
+    // rows TMA cannot read) take an FP16 widening from scratch
+    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && p->tc.raw_kb == 0;
     if (ct) need += (n_samp * sb + 255) / 256 * 256;
     if (expand) need += n_samp * 4;
     if (need) {

@@ -53,6 +53,10 @@ struct TcConfig {
     int n_groups = 1;
     int smem = 0;
     bool fast_windows = true;   // T_int % 16 == 0
+    // 8/4-bit inputs widened inside the resident-weight kernel: raw bytes of one
+    // 128-byte FP16 K block per sample row (64 for int8, 32 for 4-bit), else 0
+    // (FP16/BF16/FP8 inputs, or integer rows whose stride TMA cannot read)
+    int raw_kb = 0;
 };
 
 struct TcArgs {

@@ -97,7 +97,7 @@ extern "C" bf_status bf_execute_nct_static(bf_plan *p, const void *x, int T, flo
     const size_t turned = (n_samp * dtype_sample_bytes(p->dtype) + 255) / 256 * 256;
     // 8/4-bit inputs: the resident-weight kernel widens them itself; the
     // streamed pipeline reads an FP16 widening from the scratch
-    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && p->tc.stream;
+    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && p->tc.raw_kb == 0;
     const size_t need = turned + (expand ? n_samp * 4 : 0);
     if (need > kStaticScratchBytes)
         return set_error(BF_ERR_ARG, "input needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +

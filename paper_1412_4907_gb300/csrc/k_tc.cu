@@ -24,19 +24,20 @@ static int gcd_i(int x, int y)
 }
 
 static int stage_bytes() { return kStageDepth * kBeamsPerMTile * kMaxWinPerTile * (int)sizeof(float); }
-static int ctrl_bytes() { return 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * 16 + 2 * kStageDepth) + 16; }
+static int ctrl_bytes() { return 8 * (3 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * 16 + 2 * kStageDepth) + 16; }
 
 // End of the kernel's shared-memory layout for a configuration, computed the
 // way the kernel computes its offsets (1024 bytes of alignment slack, voltage
-// or K-block stages, resident weight slots, staging ring, barriers, TMEM
-// holder and abort flag).
+// stages, resident weight slots, the raw tile of integer inputs, staging ring,
+// barriers, TMEM holder and abort flag).
 static size_t layout_end(const TcConfig &c, int kb)
 {
     const size_t x_stage = (size_t)kb * c.nt * 128;
     const size_t gmax = (size_t)c.group;
     const size_t w_slot = (size_t)kb * 16384;
-    return 1024 + (size_t)c.xst * x_stage + gmax * w_slot + (size_t)stage_bytes() +
-           8 * (size_t)(2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * gmax + 2 * kStageDepth) + 8;
+    const size_t raw_tile = (size_t)kb * c.nt * c.raw_kb;
+    return 1024 + (size_t)c.xst * x_stage + raw_tile + gmax * w_slot + (size_t)stage_bytes() +
+           8 * (size_t)(3 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * gmax + 2 * kStageDepth) + 8;
 }
 
 static bool layout_ok(const TcConfig &c, int kb)
@@ -55,6 +56,12 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
         return false;
     }
     const int mt = f.m_pad / kRowsPerMTile;
+    // 8/4-bit inputs are widened inside the kernel when TMA can read their
+    // rows (a row stride that is a multiple of 16 bytes); otherwise they are
+    // widened to FP16 in a pass before the kernel
+    int raw_kb = 0;
+    if (p->dtype == BF_CI8 && (2 * p->N) % 16 == 0) raw_kb = 64;
+    if (p->dtype == BF_CI4 && p->N % 16 == 0) raw_kb = 32;
     if (f.kb >= 4) {
         // many antennas: the weights do not stay resident; the batched kernel's
         // streamed pipeline (k_batch.cu, one job) runs the plan with this tile
@@ -83,6 +90,7 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
         if (req.tile_t && nt != req.tile_t) continue;
         if (nt / t_int > kMaxWinPerTile) continue;   // staged window powers per tile
         const int x_stage = f.kb * nt * 128;
+        const int raw_tile = f.kb * nt * raw_kb;   // integer inputs: one raw tile beside the stages
         const int w_slot = f.kb * 16384;
         // default: the fewest weight groups per channel (each group re-reads the
         // voltage tile), then the most voltage stages in flight; a request fixes
@@ -91,7 +99,7 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
         TcConfig best;
         for (int xst = kMaxXStages; xst >= 2; --xst) {
             if (req.x_stages && xst != req.x_stages) continue;
-            const int fixed = xst * x_stage + stage_bytes() + ctrl_bytes() + 1024;
+            const int fixed = xst * x_stage + raw_tile + stage_bytes() + ctrl_bytes() + 1024;
             const int avail = kSmemLimit - fixed;
             if (avail < w_slot) continue;
             int g = std::min(mt, std::min(16, avail / w_slot));
@@ -102,6 +110,7 @@ bool tc_choose(bf_plan *p, const TcRequest &req, TcConfig *cfg, std::string *why
             TcConfig c;
             c.nt = nt;
             c.xst = xst;
+            c.raw_kb = raw_kb;
             c.nsplit = ((nt / 2) % 16 == 0 && (nt / 2) % t_int == 0) ? 2 : 1;
             c.fast_windows = (t_int % 16) == 0;
             c.n_groups = (mt + g - 1) / g;
@@ -137,9 +146,10 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
         return cudaErrorInvalidConfiguration;
     }
     CUtensorMap xm, wm;
-    const bool widen = p->dtype == BF_CI8 || p->dtype == BF_CI4;   // raw integer samples, widened in the kernel
-    memset(&xm, 0, sizeof(xm));
-    if (!widen && !encode_voltage_map(&xm, ta.x, 2 * p->N, ta.T, ta.c_launch, f.es, f.ke, cfg.nt)) {
+    const bool widen = cfg.raw_kb > 0;   // raw integer samples, widened in the kernel
+    const int row_bytes = p->N * (p->dtype == BF_CI8 ? 2 : 1);
+    if (widen ? !encode_raw_map(&xm, ta.x, row_bytes, ta.T, ta.c_launch, cfg.raw_kb, cfg.nt)
+              : !encode_voltage_map(&xm, ta.x, 2 * p->N, ta.T, ta.c_launch, f.es, f.ke, cfg.nt)) {
         *why = "voltage tensor map rejected (pointer or row stride not 16-byte aligned?)";
         return cudaErrorInvalidValue;
     }
@@ -180,8 +190,8 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
     ka.err = p->d_err;
-    ka.xraw = widen ? (const uint8_t *)ta.x : nullptr;
-    ka.n_ant = p->N;
+    ka.raw_kb = cfg.raw_kb;
+    ka.raw_stage_bytes = (uint32_t)(f.kb * cfg.nt * cfg.raw_kb);
     if (ka.ct_total == 0) return cudaSuccess;
     if (!layout_ok(cfg, f.kb) || ka.gmax != cfg.group) {   // final guard before launch
         *why = "internal tiling inconsistency (shared-memory layout exceeds the allocation)";
@@ -195,7 +205,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const int win = (ta.t_int == 64 || ta.t_int == 32 || ta.t_int == 16) ? ta.t_int : (ta.t_int % 16 == 0 ? 0 : -1);
 const bool cpx = ta.complex_out != 0;
     if (f8) return launch_tc_family<true, 0>(xm, wm, ka, win, cpx, grid, cfg.smem, s);
-    switch (p->dtype) {
+    switch (widen ? p->dtype : 0) {
     case BF_CI8: return launch_tc_family<false, BF_CI8>(xm, wm, ka, win, cpx, grid, cfg.smem, s);
     case BF_CI4: return launch_tc_family<false, BF_CI4>(xm, wm, ka, win, cpx, grid, cfg.smem, s);
     default: return launch_tc_family<false, 0>(xm, wm, ka, win, cpx, grid, cfg.smem, s);

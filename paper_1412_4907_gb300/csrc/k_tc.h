@@ -22,8 +22,8 @@ struct TcKernelArgs {
     const float *wsig;     // [C][b_pad] sigma
     float *out;
     unsigned *err;
-    const uint8_t *xraw;   // 8/4-bit inputs: [C_launch][T][N] samples, widened in the kernel
-    int n_ant;
+    uint32_t raw_stage_bytes;   // 8/4-bit inputs: raw bytes of one voltage tile (kb x nt x raw_kb), else 0
+    int raw_kb;                 // raw bytes of one K block per sample row (64 int8, 32 4-bit)
 };
 
 // Launches the variant for window specialisation win (16, 32, 64 = T_int;

@@ -72,9 +72,11 @@ __device__ __forceinline__ void group_tiles(const TcKernelArgs &a, int g, int &m
 // -1 = any T_int (per-column window counter).
 // Plans whose weights do not fit in shared memory (K >= 4 blocks) run the
 // batched kernel's streamed pipeline instead (k_batch.cu).
-// IN: BF_CI8 or BF_CI4 for integer inputs (a converter warp after the store
-// warp, and with DIRECT the idle store warp too, widen each voltage tile into
-// its stage; the producer loads weights only), else 0 (voltage tiles by TMA).
+// IN: BF_CI8 or BF_CI4 for integer inputs: the producer loads each raw tile
+// by TMA (xmap is then the raw byte map) into one raw buffer, and a converter
+// warp after the store warp (with DIRECT the idle store warp too) widens it
+// into the next FP16 voltage stage and hands the buffer back; else 0
+// (FP16/BF16/FP8 voltage tiles straight from TMA).
 template <bool F8, int WIN, bool COMPLEX, bool DIRECT, int IN>
 __global__ void __maxnreg__(96)
     k_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap, const TcKernelArgs a)
@@ -85,7 +87,9 @@ __global__ void __maxnreg__(96)
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t sx = base;
     const uint32_t sw = sx + a.xst * a.x_stage_bytes;
-    float *stage = reinterpret_cast<float *>(gbase + a.xst * a.x_stage_bytes + a.gmax * a.w_slot_bytes);
+    const uint32_t sr = sw + a.gmax * a.w_slot_bytes;   // the raw tile of integer inputs
+    float *stage = reinterpret_cast<float *>(gbase + a.xst * a.x_stage_bytes + a.gmax * a.w_slot_bytes +
+                                             a.raw_stage_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kStageDepth * kBeamsPerMTile * kMaxWinPerTile);
     const uint32_t b_xfull = smem_u32(bars + 0);                 // [kMaxXStages]
     const uint32_t b_xempty = smem_u32(bars + kMaxXStages);      // [kMaxXStages]
@@ -96,8 +100,10 @@ __global__ void __maxnreg__(96)
     const uint32_t b_wempty = b_wfull + 8 * a.gmax;               // [gmax]
     const uint32_t b_sfull = b_wempty + 8 * a.gmax;               // [stage]: every slice staged
     const uint32_t b_sempty = b_sfull + 8 * kStageDepth;          // [stage]: written out
-    uint32_t *tmem_holder =
-        reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * a.gmax + 2 * kStageDepth);
+    const uint32_t b_rfull = b_sempty + 8 * kStageDepth;          // raw tile landed
+    const uint32_t b_rempty = b_rfull + 8;                        // raw tile widened
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 3 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * a.gmax +
+                                                         2 * kStageDepth);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -108,6 +114,8 @@ __global__ void __maxnreg__(96)
             mbar_init(b_xfull + 8 * i, IN ? kConvWarps + (DIRECT ? 1 : 0) : 1);   // converters, or the TMA
             mbar_init(b_xempty + 8 * i, 1);
         }
+        mbar_init(b_rfull, 1);
+        mbar_init(b_rempty, kConvWarps + (DIRECT ? 1 : 0));
         for (int i = 0; i < a.nacc; ++i) {
             mbar_init(b_tfull + 8 * i, 1);
             mbar_init(b_tempty + 8 * i, 8);   // the 8 warps of one group release each use
@@ -123,7 +131,7 @@ __global__ void __maxnreg__(96)
         }
         *abort_flag = 0;
         fence_mbar_init();
-        if (!IN) prefetch_tensormap(&xmap);
+        prefetch_tensormap(&xmap);
         prefetch_tensormap(&wmap);
     }
     if (warp == 1) tmem_alloc(smem_u32(tmem_holder), kTmemCols);
@@ -143,7 +151,8 @@ __global__ void __maxnreg__(96)
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t xcnt = 0, wcnt = 0, x_issued = 0, w_issued = 0;
+            uint32_t xcnt = 0, wcnt = 0, x_issued = 0, w_issued = 0, rcnt = 0;
+            bool r_issued = false;
             int xs = 0;
             bool ok = true;
             for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
@@ -151,7 +160,17 @@ __global__ void __maxnreg__(96)
                 group_tiles(a, g, m0, gs);
                 int c = c_first, tt = tt_first;
                 for (long long ct = ct0; ct < ct1; ++ct) {
-                    if (!IN) {   // integer inputs: the converter warps fill the voltage stages
+                    if (IN) {   // the raw tile, once the converters have widened the last one
+                        if (!mbar_wait(b_rempty, (rcnt & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                            ok = false;
+                            break;
+                        }
+                        ++rcnt;
+                        r_issued = true;
+                        mbar_arrive_expect_tx(b_rfull, a.raw_stage_bytes);
+                        for (int kb = 0; kb < a.kb; ++kb)
+                            tma_load_3d(sr + kb * a.nt * a.raw_kb, &xmap, b_rfull, kb * a.raw_kb, tt * a.nt, c);
+                    } else {
                         if (!mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err,
                                        kWaitLimitCycles)) {
                             ok = false;
@@ -190,6 +209,7 @@ __global__ void __maxnreg__(96)
             if (*abort_flag) {   // let every issued copy land before the CTA exits
                 for (int i = 0; i < a.xst; ++i)
                     if (x_issued & (1u << i)) drain_wait(b_xfull + 8 * i, ((xcnt >> i) & 1u) ^ 1u);
+                if (r_issued) drain_wait(b_rfull, (rcnt - 1) & 1u);
                 for (int s = 0; s < a.gmax; ++s)
                     if (w_issued & (1u << s)) drain_wait(b_wfull + 8 * s, ((wcnt >> s) & 1u) ^ 1u);
             }
@@ -508,35 +528,33 @@ __global__ void __maxnreg__(96)
         }
     } else if (IN && (warp > kStoreWarp || (DIRECT && warp == kStoreWarp))) {
         // ------------------------------------------------------ converter warps
-        // widen each (channel, time tile) of 8/4-bit voltages into the next
-        // voltage stage, in the producer's order; then publish the stage
+        // for each (channel, time tile), in the producer's order: wait for the
+        // raw tile, widen its K blocks into the voltage stage, publish it
         constexpr int nconv = (kConvWarps + (DIRECT ? 1 : 0)) * 32;
         const int tid = (warp - kStoreWarp - (DIRECT ? 0 : 1)) * 32 + lane;
-        const size_t row_bytes = (size_t)a.n_ant * (IN == BF_CI8 ? 2 : 1);
-        uint32_t xcnt = 0;
+        const uint8_t *raw = gbase + (size_t)a.xst * a.x_stage_bytes + (size_t)a.gmax * a.w_slot_bytes;
+        uint32_t rcnt = 0, xcnt = 0;
         int xs = 0;
         bool ok = true;
         for (int g = gq0; g < a.n_groups && ok; g += a.gq) {
-            int c = c_first, tt = tt_first;
             for (long long ct = ct0; ct < ct1; ++ct) {
-                if (!mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
+                if (!mbar_wait(b_rfull, rcnt & 1u, abort_flag, a.err, kWaitLimitCycles) ||
+                    !mbar_wait(b_xempty + 8 * xs, ((xcnt >> xs) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                     ok = false;
                     break;
                 }
+                ++rcnt;
                 xcnt ^= 1u << xs;
-                const uint8_t *src = a.xraw + (size_t)c * a.T * row_bytes;
                 uint8_t *dst = gbase + (size_t)xs * a.x_stage_bytes;
                 for (int kb = 0; kb < a.kb; ++kb)
-                    widen_block<IN>(src, tt * a.nt, a.T, a.n_ant, kb, a.nt, dst + (size_t)kb * a.nt * 128, tid,
-                                    nconv);
+                    widen_block_smem<IN>(raw + (size_t)kb * a.nt * a.raw_kb, dst + (size_t)kb * a.nt * 128, a.nt,
+                                         tid, nconv);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_rempty);   // the raw buffer is read: the next tile may land
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(b_xfull + 8 * xs);
                 if (++xs == a.xst) xs = 0;
-                if (++tt == a.t_tiles) {
-                    tt = 0;
-                    ++c;
-                }
             }
         }
     } else if (warp == kStoreWarp && !COMPLEX && !DIRECT) {

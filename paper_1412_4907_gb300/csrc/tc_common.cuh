@@ -109,44 +109,30 @@ __device__ __forceinline__ uint4 widen_i4x4(uint32_t w)
     return make_uint4(r[0], r[1], r[2], r[3]);
 }
 
-// Widens one 128-byte K block of a voltage tile: rows t0 .. t0 + nt - 1 of one
-// channel (src: that channel's row 0; rows before 0 or at or beyond T read as
-// zero),
-// antennas 32 kb .. 32 kb + 31 (those at or beyond N read as zero), written
-// to dst as nt rows of 128 bytes with the 128-byte swizzle the MMA descriptor
-// expects (16-byte chunk j of row r at chunk j ^ (r & 7)).  Each thread
-// (tid of nthr) takes 16-byte chunks, four loads in flight.  DT: BF_CI8
-// (rows of 2N bytes) or BF_CI4 (rows of N bytes); N % 4 == 0.
+// Widens one 128-byte K block of a voltage tile from its raw copy in shared
+// memory (nt rows of RAW_KB bytes, as TMA lands them: out-of-range rows and
+// antennas are zero bytes, which widen to 0) into nt swizzled FP16 rows of
+// 128 bytes.  Each thread takes 16 raw bytes at a time: 8 antennas (int8) or
+// 16 antennas (4-bit), i.e. 2 or 4 output chunks of 16 bytes.
 template <int DT>
-__device__ __forceinline__ void widen_block(const uint8_t *__restrict__ src, int t0, int T, int N, int kb, int nt,
-                                            uint8_t *dst, int tid, int nthr)
+__device__ __forceinline__ void widen_block_smem(const uint8_t *raw, uint8_t *dst, int nt, int tid, int nthr)
 {
-    constexpr int kBytes = DT == BF_CI8 ? 8 : 4;   // source bytes per 4 antennas
-    const size_t row_bytes = (size_t)N * (DT == BF_CI8 ? 2 : 1);
-    const int n_items = nt * 8;
-    for (int i0 = tid; i0 < n_items; i0 += 4 * nthr) {
-        uint2 w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * nthr;
-            const int row = i >> 3, ch = i & 7;
-            const int t = t0 + row, a4 = kb * 32 + ch * 4;   // first antenna of the chunk
-            w[u] = make_uint2(0u, 0u);
-            if (i < n_items && (unsigned)t < (unsigned)T && a4 < N) {
-                const uint8_t *q = src + (size_t)t * row_bytes + (size_t)a4 * (kBytes / 4);
-                if (DT == BF_CI8) w[u] = __ldg(reinterpret_cast<const uint2 *>(q));
-                else w[u].x = __ldg(reinterpret_cast<const uint32_t *>(q));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * nthr;
-            if (i >= n_items) break;
-            const int row = i >> 3, ch = i & 7;
-            const int t = t0 + row, a4 = kb * 32 + ch * 4;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if ((unsigned)t < (unsigned)T && a4 < N) v = DT == BF_CI8 ? widen_i8x4(w[u]) : widen_i4x4(w[u].x);
-            *reinterpret_cast<uint4 *>(dst + row * 128 + ((ch ^ (row & 7)) << 4)) = v;
+    constexpr int kRawKb = DT == BF_CI8 ? 64 : 32;     // raw bytes per row of the K block
+    constexpr int kPieces = kRawKb / 16;                // 16-byte raw pieces per row
+    const int n_items = nt * kPieces;
+    for (int i = tid; i < n_items; i += nthr) {
+        const int row = i / kPieces, pc = i % kPieces;
+        const uint4 v = *reinterpret_cast<const uint4 *>(raw + row * kRawKb + pc * 16);
+        uint8_t *drow = dst + row * 128;
+        const int sw = row & 7;
+        if (DT == BF_CI8) {
+            *reinterpret_cast<uint4 *>(drow + (((2 * pc) ^ sw) << 4)) = widen_i8x4(make_uint2(v.x, v.y));
+            *reinterpret_cast<uint4 *>(drow + (((2 * pc + 1) ^ sw) << 4)) = widen_i8x4(make_uint2(v.z, v.w));
+        } else {
+            *reinterpret_cast<uint4 *>(drow + (((4 * pc) ^ sw) << 4)) = widen_i4x4(v.x);
+            *reinterpret_cast<uint4 *>(drow + (((4 * pc + 1) ^ sw) << 4)) = widen_i4x4(v.y);
+            *reinterpret_cast<uint4 *>(drow + (((4 * pc + 2) ^ sw) << 4)) = widen_i4x4(v.z);
+            *reinterpret_cast<uint4 *>(drow + (((4 * pc + 3) ^ sw) << 4)) = widen_i4x4(v.w);
         }
     }
 }

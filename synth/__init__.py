@@ -273,14 +273,21 @@ def config1() -> tuple[Scene, np.ndarray, int]:
     return scene, dirs, 16
 
 
-def config2() -> tuple[Scene, np.ndarray, int]:
+def config2(sigma: float | None = None) -> tuple[Scene, np.ndarray, int]:
     """Real-time-shaped FP16 case: BEST-2 grid, 1024 channels over 16 MHz,
     1024 beams (32 x 32 over +-10 deg), T = 15625, noise plus 3 sources of
-    random direction and SNR 0-20 dB, T_int = 64."""
+    random direction and SNR 0-20 dB, T_int = 64.  ``sigma``: noise standard
+    deviation per component for integer-input variants of the same chunk
+    (16 for 8-bit, 2 for 4-bit samples); the default is CN(0, 1) noise."""
     dirs = beam_grid(32, 32, 10.0)
-    scene = Scene(pos=grid_positions(), freqs=channel_freqs(400e6, 16e6, 1024),
-                  n_samp=15625, seed=2,
-                  sources=random_sources(3, 10.0, 0.0, 20.0, 1.0, 2))
+    if sigma is None:
+        scene = Scene(pos=grid_positions(), freqs=channel_freqs(400e6, 16e6, 1024),
+                      n_samp=15625, seed=2,
+                      sources=random_sources(3, 10.0, 0.0, 20.0, 1.0, 2))
+    else:
+        scene = Scene(pos=grid_positions(), freqs=channel_freqs(400e6, 16e6, 1024),
+                      n_samp=15625, seed=2, noise_sigma=sigma,
+                      sources=random_sources(3, 10.0, 0.0, 20.0, 2 * sigma ** 2, 2))
     return scene, dirs, 64
 
 
