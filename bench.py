@@ -356,8 +356,21 @@ def run_ours(args):
         ms32 = a.elapsed_time(b_) / n32
         p32.close()
         del x32
-        fp32 = {"value": F / (ms32 * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": ms32, "dtype": "f32",
-                "kernel": "k_simt (FP32 FFMA)"}
+        # the FFMA peak measured now, with the SM clock sampled during the probe
+        probe_clk = ClockSampler(local)
+        probe_clk.start()
+        time.sleep(0.3)
+        probe_clk.mark_start()
+        ffma = bf.bf_measure_ffma(1.0)
+        probe_clk.mark_stop()
+        pclk = probe_clk.stop()
+        tf32 = F / (ms32 * 1e-3) / 1e12
+        fp32 = {"value": tf32, "unit": UNIT, "ms_per_step": ms32, "dtype": "f32",
+                "kernel": "k_simt_pipe (FP32 FFMA)",
+                "roofline": {"bound": "alu", "achieved": tf32, "peak": ffma, "unit": "TFLOP/s", "frac": tf32 / ffma,
+                             "peak_source": "bf_measure_ffma: independent FFMA chains on every SM, 1 s, measured "
+                                            "in this run",
+                             "peak_clock_sm_mhz": pclk["sm_mhz"] if pclk else None}}
 
     if rank != 0:
         plan.close()

@@ -468,6 +468,15 @@ bf_status bf_detect(const float *d_power, int n_beam, int n_chan, int n_win, flo
 bf_status bf_selftest_timeout(double limit_ms, void *stream);
 
 /*
+ * bf_measure_ffma — measurement aid, not part of the paper's method: the FP32
+ * FFMA rate of the current GPU (independent FFMA chains on every SM for about
+ * `seconds`), the peak the plain FP32 form (BF_C32) is held against.
+ *  seconds  in (0, 60];  tflops  host, receives FLOP/s / 1e12 (2 FLOP per FFMA).
+ * Synchronous; allocates and frees a small device buffer.  Errors: BF_ERR_ARG.
+ */
+bf_status bf_measure_ffma(double seconds, double *tflops, void *stream);
+
+/*
  * bf_execute_nct_static — bf_execute for an antenna-major (BF_LAYOUT_NCT)
  * tensor-core plan that allocates nothing.  The paper has no counterpart: it
  * exists for callers that cannot allocate device memory when they execute

@@ -81,6 +81,7 @@ SIGNATURES = {
     "bf_server_now": [],
     "bf_detect": [_P, _I, _I, _I, ctypes.c_float, _P, _P, _I, _P, _P],
     "bf_selftest_timeout": [ctypes.c_double, _P],
+    "bf_measure_ffma": [ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P],
     "bf_execute_nct_static": [_P, _P, _I, _P, _P],
 }
 
@@ -313,6 +314,13 @@ def detect(power, k_sigma: float, max_hits: int = 1 << 16, want_z: bool = True, 
 
 def bf_selftest_timeout(limit_ms: float = 50.0, stream: int = 0):
     _check(_lib.bf_selftest_timeout(float(limit_ms), stream or None))
+
+
+def bf_measure_ffma(seconds: float = 1.0, stream: int = 0) -> float:
+    """The GPU's FP32 FFMA rate in TFLOP/s (a measurement aid)."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.bf_measure_ffma(float(seconds), ctypes.byref(v), stream or None))
+    return v.value
 
 
 # ------------------------------------------------------------ torch helper

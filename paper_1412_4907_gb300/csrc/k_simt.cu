@@ -5,9 +5,11 @@
 // (the static-beam reuse of Section 2.1).
 //
 // Block: 64 beams x 64 samples of one channel, 256 threads, each thread a
-// 4-beam x 4-sample register tile; antennas are staged through shared memory
-// 16 at a time.  In power mode a block owns whole integration windows and
-// sums |B|^2 of each window in ascending sample order (deterministic).
+// 4-beam x 4-sample register tile.  Two forms: a pipelined one (below) for
+// complex beams and for windows of 16, 32 or 64 samples, and a general one
+// for any other T_int, in which antennas are staged through shared memory 16
+// at a time and a block owns whole integration windows, summing |B|^2 of
+// each window in ascending sample order (deterministic).
 #include "bf_internal.h"
 
 namespace bfi {
@@ -138,11 +140,190 @@ __global__ void __launch_bounds__(256) k_simt(const float2 *__restrict__ X, cons
     }
 }
 
+// ------------------------------------------------------------ pipelined form
+// 128 beams x 64 samples per block, each thread an 8-beam x 4-sample register
+// tile (6 shared-memory loads per 128 FFMA); a block walks a run of
+// 64-sample sub-tiles of one channel and beam block, and its operands come in
+// through a two-stage cp.async pipeline: antenna chunks of kKA (voltages, and
+// weights unless the whole weight tile is resident, N <= kKA) for the next
+// step land while the current one is multiplied.  Used for complex beams and
+// for powers whose windows (T_int = WIN of 16, 32 or 64) divide a sub-tile:
+// each thread squares its 4 samples of 4 beams and the window sums are
+// reduced across the WIN / 4 lanes that hold the window, in a fixed order.
+constexpr int kKA = 32;   // antennas per pipeline step
+constexpr int kRun = 16;  // sub-tiles (1024 samples) per block
+constexpr int kPB = 128;  // beams per block of the pipelined form
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <bool NCT, bool COMPLEX, int WIN>
+__global__ void __launch_bounds__(256, 2)
+    k_simt_pipe(const float2 *__restrict__ X, const float2 *__restrict__ W, float *__restrict__ out, int N,
+                int c_base, int c_in_stride, int c_total, int B, int b_pad, int T, int T_o, int t_end)
+{
+    // dynamic shared memory (100 KB): two stages of voltages and of weights
+    extern __shared__ __align__(16) float2 pipe_smem[];
+    auto sX = reinterpret_cast<float2(*)[kKA][kST + kPad]>(pipe_smem);
+    auto sW = reinterpret_cast<float2(*)[kKA][kPB + kPad]>(pipe_smem + 2 * kKA * (kST + kPad));
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int c = blockIdx.z;
+    const int cg = c_base + c;
+    const int b0 = blockIdx.y * kPB;
+    const int sub0 = blockIdx.x * kRun;
+    const int n_sub = min(kRun, (t_end - sub0 * kST + kST - 1) / kST);
+    const int n_chunk = (N + kKA - 1) / kKA;
+    const bool w_resident = n_chunk == 1;
+    const int n_step = n_sub * n_chunk;
+    const float2 *Wc = W + ((size_t)cg * b_pad + b0) * N;
+
+    // issue the copies of step q (sub-tile q / n_chunk, antenna chunk q % n_chunk) into stage q & 1
+    auto load = [&](int q) {
+        const int st = q & 1;
+        const int sub = sub0 + q / n_chunk, a0 = (q % n_chunk) * kKA;
+        const int t0 = sub * kST;
+        for (int i = tid; i < kKA * kST; i += 256) {
+            int a, tl;
+            if (NCT) {
+                a = i / kST;
+                tl = i % kST;
+            } else {
+                tl = i / kKA;
+                a = i % kKA;
+            }
+            const int t = t0 + tl, an = a0 + a;
+            const bool ok = an < N && t < t_end;
+            const float2 *src = NCT ? X + ((size_t)(ok ? an : 0) * c_in_stride + c) * T + (ok ? t : 0)
+                                    : X + ((size_t)c * T + (ok ? t : 0)) * N + (ok ? an : 0);
+            cp_async8(&sX[st][a][tl], src, ok);
+        }
+        if (!w_resident || q == 0)
+            for (int i = tid; i < kKA * kPB; i += 256) {
+                const int bl = i / kKA, a = i % kKA;
+                const bool ok = a0 + a < N && b0 + bl < b_pad;   // rows past the padded beams read zero
+                cp_async8(&sW[st][a][bl], Wc + (ok ? (size_t)bl * N + a0 + a : 0), ok);
+            }
+        cp_async_commit();
+    };
+
+    float2 acc[8][4];
+    load(0);
+    for (int q = 0; q < n_step; ++q) {
+        if (q + 1 < n_step) {
+            load(q + 1);
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();
+        const int st = q & 1, k = q % n_chunk;
+        const int ws = w_resident ? 0 : st;
+        if (k == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 1
+        for (int a = 0; a < kKA; ++a) {
+            float2 w[8];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float4 v = *reinterpret_cast<const float4 *>(&sW[ws][a][8 * ty + 2 * h]);
+                w[2 * h] = make_float2(v.x, v.y);
+                w[2 * h + 1] = make_float2(v.z, v.w);
+            }
+            const float4 x01 = *reinterpret_cast<const float4 *>(&sX[st][a][4 * tx]);
+            const float4 x23 = *reinterpret_cast<const float4 *>(&sX[st][a][4 * tx + 2]);
+            const float2 x[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
+                                 make_float2(x23.z, x23.w)};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(w[i].x, x[j].x, acc[i][j].x);
+                    acc[i][j].x = fmaf(-w[i].y, x[j].y, acc[i][j].x);
+                    acc[i][j].y = fmaf(w[i].x, x[j].y, acc[i][j].y);
+                    acc[i][j].y = fmaf(w[i].y, x[j].x, acc[i][j].y);
+                }
+        }
+        if (k == n_chunk - 1) {
+            const int t_sub = (sub0 + q / n_chunk) * kST;
+            if (COMPLEX) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int b = b0 + 8 * ty + i;
+                    if (b >= B) continue;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int t = t_sub + 4 * tx + j;
+                        if (t < t_end) reinterpret_cast<float2 *>(out)[((size_t)b * c_total + cg) * T + t] = acc[i][j];
+                    }
+                }
+            } else {
+                constexpr int L = WIN / 4;   // lanes per window
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float pw = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) pw = fmaf(acc[i][j].x, acc[i][j].x, fmaf(acc[i][j].y, acc[i][j].y, pw));
+#pragma unroll
+                    for (int m = 1; m < L; m <<= 1) pw += __shfl_xor_sync(0xffffffffu, pw, m);
+                    const int b = b0 + 8 * ty + i, j = (t_sub + 4 * tx) / WIN;
+                    if ((tx % L) == 0 && b < B && j < T_o) out[((size_t)b * c_total + cg) * T_o + j] = pw;
+                }
+            }
+        }
+        __syncthreads();   // the stage is free for step q + 2
+    }
+}
+
 cudaError_t launch_simt_range(bf_plan *p, const void *x, int c_base, int c_launch, int T, float *out,
                               int complex_out, cudaStream_t s)
 {
     const bool nct = p->layout == BF_LAYOUT_NCT;
     const int T_o = T / p->t_int;
+    const int t_int = p->t_int;
+    if (complex_out || t_int == 16 || t_int == 32 || t_int == 64) {
+        // pipelined form: complex beams (every sample) or powers of whole windows
+        const int t_end = complex_out ? T : T_o * t_int;
+        const int n_sub = (t_end + kST - 1) / kST;
+        if (n_sub == 0 || c_launch == 0) return cudaSuccess;
+        dim3 grid((n_sub + kRun - 1) / kRun, (p->wf.b_pad + kPB - 1) / kPB, c_launch);
+        const float2 *X = reinterpret_cast<const float2 *>(x);
+        const float2 *W = reinterpret_cast<const float2 *>(p->d_w);
+        const int c_in_stride = nct ? p->C : c_launch;
+        const int pipe_smem = (int)(sizeof(float2) * 2 * kKA * ((kST + kPad) + (kPB + kPad)));
+#define BF_SIMT_PIPE(NCTV, CPX, WV)                                                                            \
+    do {                                                                                                       \
+        cudaError_t e_ = cudaFuncSetAttribute(k_simt_pipe<NCTV, CPX, WV>,                                      \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, pipe_smem);         \
+        if (e_ != cudaSuccess) return e_;                                                                      \
+        k_simt_pipe<NCTV, CPX, WV><<<grid, 256, pipe_smem, s>>>(X, W, out, p->N, c_base, c_in_stride, p->C, p->B, \
+                                                            p->wf.b_pad, T, T_o, t_end);                       \
+    } while (0)
+#define BF_SIMT_PIPE_W(NCTV)                          \
+    do {                                              \
+        if (complex_out) BF_SIMT_PIPE(NCTV, true, 64); \
+        else if (t_int == 64) BF_SIMT_PIPE(NCTV, false, 64); \
+        else if (t_int == 32) BF_SIMT_PIPE(NCTV, false, 32); \
+        else BF_SIMT_PIPE(NCTV, false, 16);           \
+    } while (0)
+        if (nct) BF_SIMT_PIPE_W(true);
+        else BF_SIMT_PIPE_W(false);
+#undef BF_SIMT_PIPE_W
+#undef BF_SIMT_PIPE
+        return cudaGetLastError();
+    }
     const int wins = std::max(1, std::min(128, (128 + p->t_int - 1) / p->t_int));
     const int nx = complex_out ? (T + 127) / 128 : (T_o + wins - 1) / wins;
     if (nx == 0 || c_launch == 0) return cudaSuccess;
