@@ -255,6 +255,10 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
         __syncwarp();
     } else if (warp == 1) {
         // ----------------------------------------------------------- MMA issuer
+        // (one issuer: a second one taking alternate units would have to skip
+        // the other's stage fills without waiting, and with units of several
+        // K blocks it can fall two phases behind on a stage, where a parity
+        // wait can no longer tell the phases apart)
         if (lane == 0) {
             uint32_t par = 0, tpar = 0;
             int st = 0, acc = 0;

@@ -108,11 +108,19 @@ __global__ void __maxnreg__(96)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // FP16/BF16/FP8 powers with the direct-store epilogue: the store warp has
+    // nothing to store, so it issues the MMAs of every other tile (the second
+    // accumulator) while warp 1 waits, commits and walks to its next tile.
+    // Both issuers wait for every voltage stage and weight slot in order (so
+    // neither runs a phase ahead of a barrier).  Integer inputs keep the store
+    // warp as a second converter: with one converter 8-bit input lost 10%.
+    constexpr bool TWO = DIRECT && IN == 0;
+    constexpr unsigned kIssuers = TWO ? 2u : 1u;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < a.xst; ++i) {
             mbar_init(b_xfull + 8 * i, IN ? kConvWarps + (DIRECT ? 1 : 0) : 1);   // converters, or the TMA
-            mbar_init(b_xempty + 8 * i, 1);
+            mbar_init(b_xempty + 8 * i, kIssuers);
         }
         mbar_init(b_rfull, 1);
         mbar_init(b_rempty, kConvWarps + (DIRECT ? 1 : 0));
@@ -120,10 +128,10 @@ __global__ void __maxnreg__(96)
             mbar_init(b_tfull + 8 * i, 1);
             mbar_init(b_tempty + 8 * i, 8);   // the 8 warps of one group release each use
         }
-        mbar_init(b_drain, 1);
+        mbar_init(b_drain, kIssuers);
         for (int s = 0; s < a.gmax; ++s) {
             mbar_init(b_wfull + 8 * s, 1);
-            mbar_init(b_wempty + 8 * s, 1);
+            mbar_init(b_wempty + 8 * s, kIssuers);
         }
         for (int i = 0; i < kStageDepth; ++i) {
             mbar_init(b_sfull + 8 * i, 4 * a.nsplit);   // the active epilogue warps
@@ -215,10 +223,14 @@ __global__ void __maxnreg__(96)
             }
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // ----------------------------------------------------------- MMA issuer
+    } else if (warp == 1 || (TWO && warp == kStoreWarp)) {
+        // ---------------------------------------------------------- MMA issuers
+        // one issuing thread, or two taking alternate tiles: each waits for
+        // every voltage stage and weight slot, issues its own tiles, and
+        // commits the stage and slot releases (barriers counting kIssuers)
         if (lane == 0) {
-            uint32_t xpar = 0, wpar = 0, tpar = 0;
+            const uint32_t par = warp == 1 ? 0u : 1u;
+            uint32_t xpar = 0, wpar = 0, tpar = 0, kt = 0;
             int xs = 0, acc = 0;
             bool ok = true;
             // Descriptor words of the first weight slot and the first voltage stage;
@@ -244,13 +256,18 @@ __global__ void __maxnreg__(96)
                         break;
                     }
                     xpar ^= 1u << xs;
-                    for (int s = 0; s < gs; ++s) {
+                    for (int s = 0; s < gs; ++s, ++kt) {
                         if (neww) {
                             if (!mbar_wait(b_wfull + 8 * s, (wpar >> s) & 1u, abort_flag, a.err, kWaitLimitCycles)) {
                                 ok = false;
                                 break;
                             }
                             wpar ^= 1u << s;
+                        }
+                        if (TWO && (kt & 1u) != par) {   // the other issuer's tile
+                            if (lastw) mma_commit(b_wempty + 8 * s);
+                            if (++acc == a.nacc) acc = 0;
+                            continue;
                         }
                         if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err,
                                        kWaitLimitCycles)) {
