@@ -120,19 +120,31 @@ __device__ __forceinline__ void widen_block_smem(const uint8_t *raw, uint8_t *ds
     constexpr int kRawKb = DT == BF_CI8 ? 64 : 32;     // raw bytes per row of the K block
     constexpr int kPieces = kRawKb / 16;                // 16-byte raw pieces per row
     const int n_items = nt * kPieces;
-    for (int i = tid; i < n_items; i += nthr) {
-        const int row = i / kPieces, pc = i % kPieces;
-        const uint4 v = *reinterpret_cast<const uint4 *>(raw + row * kRawKb + pc * 16);
-        uint8_t *drow = dst + row * 128;
-        const int sw = row & 7;
-        if (DT == BF_CI8) {
-            *reinterpret_cast<uint4 *>(drow + (((2 * pc) ^ sw) << 4)) = widen_i8x4(make_uint2(v.x, v.y));
-            *reinterpret_cast<uint4 *>(drow + (((2 * pc + 1) ^ sw) << 4)) = widen_i8x4(make_uint2(v.z, v.w));
-        } else {
-            *reinterpret_cast<uint4 *>(drow + (((4 * pc) ^ sw) << 4)) = widen_i4x4(v.x);
-            *reinterpret_cast<uint4 *>(drow + (((4 * pc + 1) ^ sw) << 4)) = widen_i4x4(v.y);
-            *reinterpret_cast<uint4 *>(drow + (((4 * pc + 2) ^ sw) << 4)) = widen_i4x4(v.z);
-            *reinterpret_cast<uint4 *>(drow + (((4 * pc + 3) ^ sw) << 4)) = widen_i4x4(v.w);
+    // four independent pieces per trip (loads first), so the byte permutes of
+    // one piece overlap the loads and stores of the others
+    for (int i0 = tid; i0 < n_items; i0 += 4 * nthr) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * nthr;
+            if (i < n_items) v[u] = *reinterpret_cast<const uint4 *>(raw + (i / kPieces) * kRawKb + (i % kPieces) * 16);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * nthr;
+            if (i >= n_items) break;
+            const int row = i / kPieces, pc = i % kPieces;
+            uint8_t *drow = dst + row * 128;
+            const int sw = row & 7;
+            if (DT == BF_CI8) {
+                *reinterpret_cast<uint4 *>(drow + (((2 * pc) ^ sw) << 4)) = widen_i8x4(make_uint2(v[u].x, v[u].y));
+                *reinterpret_cast<uint4 *>(drow + (((2 * pc + 1) ^ sw) << 4)) = widen_i8x4(make_uint2(v[u].z, v[u].w));
+            } else {
+                *reinterpret_cast<uint4 *>(drow + (((4 * pc) ^ sw) << 4)) = widen_i4x4(v[u].x);
+                *reinterpret_cast<uint4 *>(drow + (((4 * pc + 1) ^ sw) << 4)) = widen_i4x4(v[u].y);
+                *reinterpret_cast<uint4 *>(drow + (((4 * pc + 2) ^ sw) << 4)) = widen_i4x4(v[u].z);
+                *reinterpret_cast<uint4 *>(drow + (((4 * pc + 3) ^ sw) << 4)) = widen_i4x4(v[u].w);
+            }
         }
     }
 }
