@@ -556,7 +556,9 @@ def run_batched(args):
 def batched_measure(args, emit=True):
     """Config 4: 48 sub-array jobs of uneven size (N in {16..256}, B
     log-uniform in 8..4096, C in {128, 512, 2048}, T = 4096, FP16, T_int 64)
-    in one graph-captured persistent launch.  Variants: fixed 128-sample
+    in one graph-captured batch step: the jobs of 128 and 256 antennas in one
+    persistent launch, the others in their plans' resident-weight kernel on
+    forked streams.  Variants: fixed 128-sample
     tiles, the autotuned tile width, and the jobs run one plan at a time
     through bf_execute (each with the single-plan planner's tiling); plus the
     power error on sampled channels against the oracle.  With ``emit`` one
@@ -569,6 +571,9 @@ def batched_measure(args, emit=True):
     torch.cuda.set_device(0)
     div = max(1, args.batched_chan_div)
     jobs = synth.config4_jobs(chan_choices=(128 // div, 512 // div, 2048 // div))
+    if args.batched_ant:   # a subset of the jobs by antenna count (diagnostics)
+        keep = {int(v) for v in args.batched_ant.split(",")}
+        jobs = [j for j in jobs if j.scene.pos.shape[0] in keep]
     stream = torch.cuda.Stream()
     plans, outs, n_samps = [], [], []
     F = 0.0
@@ -580,12 +585,16 @@ def batched_measure(args, emit=True):
         F += flops(N, B, C, T)
     xs = config4_inputs(jobs, torch)
     torch.cuda.synchronize()
+    # kernels per batch step: one persistent launch for the streamed-weight
+    # plans, one resident-weight launch per other plan
+    n_res = sum(bf.bf_plan_query_tiles(p.handle)["x_stages"] > 0 for p in plans)
+    step_launches = n_res + (1 if n_res < len(plans) else 0)
     pk, pk_kind = peaks()
     steps = max(3, min(args.steps, 20))
     warm = max(3, min(args.warmup, 5))
     summary = {"workload": "48 sub-array jobs: N in {16,32,64,128,256} of the 256-antenna 200 m layout, "
                            "B log-uniform 8..4096, C in {128,512,2048}" + (f" / {div}" if div > 1 else "")
-                           + ", T 4096 FP16, T_int 64, one graph-captured persistent launch",
+                           + ", T 4096 FP16, T_int 64, one graph-captured batch step",
                "total_tflop": F / 1e12, "steps": steps, "warmup": warm}
 
     def timed(run):
@@ -627,7 +636,7 @@ def batched_measure(args, emit=True):
     batch.capture()
     ms_fixed = timed(batch.replay)
     batch.sync()
-    line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": 1}, "fixed_128")
+    line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": step_launches}, "fixed_128")
     batch.close()
     # autotuned
     tuned = tune.tune_batch(plans, xs, outs, n_samps, stream=stream, reps=3, cache=None)
@@ -638,7 +647,8 @@ def batched_measure(args, emit=True):
     ms_tuned = timed(batch.replay)
     batch.sync()
     line("batched, autotuned tile", ms_tuned, {"tile_t": tuned["tile_t"], "tuning_table": tuned["table"],
-                                                "speedup_vs_fixed": ms_fixed / ms_tuned, "gpu_launches_per_step": 1},
+                                                "speedup_vs_fixed": ms_fixed / ms_tuned,
+                                                "gpu_launches_per_step": step_launches},
          "autotuned")
     # one plan at a time
     def per_plan():
@@ -1025,6 +1035,8 @@ def main():
                     help="batched uneven launch of 48 sub-array jobs (one JSON line per variant)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak: every rank beamforms its own chunk; strong: the chunk's channels are split over ranks")
+    ap.add_argument("--batched-ant", default="",
+                    help="batched: only the jobs with these antenna counts (comma list; diagnostics)")
     ap.add_argument("--batched-chan-div", type=int, default=1,
                     help="divide every job's channel count (smaller case of the same jobs, for profiling)")
     ap.add_argument("--peaks", action="store_true",

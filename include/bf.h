@@ -26,7 +26,10 @@
  *    throws across the ABI.
  *  - Device-side waits are bounded; a wait that gives up records
  *    BF_ERR_TIMEOUT in the plan, reported by the next bf_sync.
- *  - A plan may be used by one host thread at a time.
+ *  - A plan may be used by one host thread at a time, and its executes run
+ *    one after another on the device: they share the plan's scratch, so
+ *    executes of one plan on different streams must be ordered (events) by
+ *    the caller.
  */
 #ifndef BF_H
 #define BF_H
@@ -268,13 +271,18 @@ bf_status bf_corner_turn(const void *d_in, int in_dtype, void *d_out, int out_dt
                          void *stream);
 
 /*
- * Batched execution: the jobs of several plans in ONE persistent launch.
+ * Batched execution: the jobs of several plans in one step.
  *
  * A batch groups plans that differ in antennas, beams, channels and sample
  * counts (sub-arrays, beam sets, observing modes sharing a GPU) so that a
- * step over all of them is a single kernel launch whose CTAs split the work
- * by cost (MMA K blocks per tile), instead of one under-filled launch per
- * plan.  Section 4 measures one beamformer configuration at a time; this is
+ * step over all of them is one call (and one CUDA graph replay), scheduled
+ * by job size instead of one launch per plan:
+ *  - jobs of fewer than 4 K blocks of 64 operand elements (fewer than 128
+ *    antennas at 16 bits) run their plan's resident-weight kernel, several
+ *    at a time on streams forked from the step's stream;
+ *  - the others run the streamed-weight persistent kernel: a job of at least
+ *    64 tiles per SM gets a launch to itself, and the smaller ones share one
+ *    launch whose CTAs take tiles from a work counter.  Section 4 measures one beamformer configuration at a time; this is
  * the same computation (Eq. 1 weights, Section 2.1 fused power detection)
  * applied to many configurations at once.
  *
@@ -291,8 +299,9 @@ typedef struct bf_batch bf_batch;
  * bf_batch_create — batch over plans[0 .. n_plans-1] (host array, read
  * during the call).  tile_t = 0 chooses the widest tile (samples per MMA, a
  * multiple of 16 and of T_int, at most 256 and 16 windows); otherwise that
- * width.  Allocates the device job table (one entry per plan) and a pinned
- * host copy.  Errors: BF_ERR_ARG (NULL or empty), BF_ERR_UNSUPPORTED
+ * width (of the persistent launch; resident-weight jobs keep their plan's
+ * tiling).  Allocates the device job table (one entry per plan), a pinned
+ * host copy, and the fork streams.  Errors: BF_ERR_ARG (NULL or empty), BF_ERR_UNSUPPORTED
  * (plans that cannot share a launch, no tile width fits), BF_ERR_NOMEM /
  * BF_ERR_CUDA.
  */
@@ -311,9 +320,13 @@ bf_status bf_batch_set(bf_batch *batch, int job, const void *d_voltages, int n_s
 
 /*
  * bf_batch_execute — one step over every job on `stream` (NULL = the legacy
- * default stream): integer inputs are widened to FP16 in batch-owned
- * buffers, the job table is copied up, and one persistent launch computes
- * all powers.  Asynchronous.  Errors: BF_ERR_STATE if a job was never set.
+ * default stream): the resident-weight jobs run on streams that wait for
+ * `stream` and that `stream` then waits for (8/4-bit inputs are widened in
+ * their kernel when TMA can read the rows, else in a batch-owned buffer);
+ * the other jobs' integer inputs are widened to FP16 in batch-owned buffers
+ * and persistent launches compute their powers.  Asynchronous: when
+ * `stream` has reached the step's end, every output is written.  Errors:
+ * BF_ERR_STATE if a job was never set.
  */
 bf_status bf_batch_execute(bf_batch *batch, void *stream);
 
@@ -331,9 +344,9 @@ bf_status bf_batch_replay(bf_batch *batch, void *stream);
  * device-side wait of that step gave up (the flag is then cleared). */
 bf_status bf_batch_sync(bf_batch *batch);
 
-/* bf_batch_query — tile width, work units (channel x time tile x 64-beam
- * block over all jobs) and useful FLOPs per step (8 N B C n_samp summed over
- * jobs); any output may be NULL. */
+/* bf_batch_query — tile width and work units (channel x time tile x 64-beam
+ * block) of the persistent launch, and useful FLOPs per step over all jobs
+ * (8 N B C n_samp summed); any output may be NULL. */
 bf_status bf_batch_query(const bf_batch *batch, int *tile_t, long long *units, double *flops);
 
 /* bf_batch_destroy — wait for the last step and free the batch (not the

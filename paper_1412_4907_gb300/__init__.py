@@ -425,7 +425,8 @@ class Plan:
 
 
 class Batch:
-    """Several plans stepped by one persistent launch (``bf_batch_*``).
+    """Several plans stepped together (``bf_batch_*``): one call, or one
+    CUDA graph replay, per step, scheduled by job size.
     ``set(j, x, out)`` binds job j's voltages and powers (torch tensors);
     ``execute()`` runs one step on the stream given here; ``capture()`` /
     ``replay()`` record and relaunch that step as a CUDA graph."""

@@ -34,7 +34,7 @@ struct __align__(128) BatchJob {
     float *acc_out;        // [B][C] partial sum of window T_o carried out, or NULL
 };
 
-static_assert(sizeof(BatchJob) == 384, "job table rows are 384 bytes (16 fit in the launch parameters)");
+static_assert(sizeof(BatchJob) == 384, "job table rows are 384 bytes (64 fit in the launch parameters)");
 
 // Launch-wide choices: tile width and the pipeline depths that follow.
 struct BatchCore {
@@ -63,14 +63,24 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
 // Numbers the units of jobs[0..n) in order; returns the total.
 long long batch_index(BatchJob *jobs, int n);
 
-// One persistent launch over the table (already in device memory).
+// One persistent launch over the table (already in device memory).  d_err:
+// status word of the device-side waits.  d_next: the launch's work counter
+// (device, 8 bytes), zeroed on `s` before the launch, so launches sharing a
+// counter must be ordered on the device; NULL: CTA i takes units i, i + G,
+// ... (G = grid size).  The counter keeps the CTAs of a launch over several
+// jobs on neighbouring units; one job alone runs faster on the fixed stride
+// (46.9 against 48.8 ms for the 20 sub-array jobs of 128 and 256 antennas of
+// the uneven-batch workload launched one at a time).
 cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
-                              unsigned *d_err, cudaStream_t s);
+                              unsigned *d_err, unsigned long long *d_next, cudaStream_t s);
 
-// Jobs a launch can take by value in its parameters (16 x 384 bytes, within
-// the 32 KB parameter space of current CUDA): no table copy, so nothing of the
-// launch waits behind other host-to-device copies.
-constexpr int kParamJobs = 16;
+// Jobs a launch can take by value in its parameters (64 x 384 bytes = 24 KB,
+// within the 32 KB parameter space of current CUDA): no table copy, so nothing
+// of the launch waits behind other host-to-device copies, and the tensor maps
+// are read from the parameter bank.  On the 20 sub-array jobs of 128 and 256
+// antennas of the uneven-batch workload a step took 48.6 ms with the table in
+// the parameters against 50.7 ms with it in device memory.
+constexpr int kParamJobs = 64;
 struct ParamJobs {
     BatchJob j[kParamJobs];
 };
@@ -79,7 +89,8 @@ struct ParamJobs {
 // value.  Used by single plans with large antenna counts (n = 1), the serving
 // loop and small batches.
 cudaError_t batch_core_launch_params(const BatchCore &core, const BatchJob *jobs, int n, long long total_units,
-                                     unsigned *d_err, cudaStream_t s);
+                                     unsigned *d_err, unsigned long long *d_next, cudaStream_t s);
+// One job alone, on the fixed stride.
 cudaError_t batch_core_launch_one(const BatchCore &core, const BatchJob &job, unsigned *d_err, cudaStream_t s);
 
 }  // namespace bfi

@@ -65,6 +65,7 @@ struct TcArgs {
     int T, T_o, t_int;
     int complex_out;
     float *out;          // power [B][C_total][T_o] or beams [B][C_total][T][2]
+    unsigned *err = nullptr;   // status word of the device-side waits (NULL: the plan's)
 };
 
 bf_status set_error(bf_status s, const std::string &msg);

@@ -3,17 +3,31 @@
 // several streams) in one launch.
 //
 // Every job keeps its own plan (weights, per-beam scales) and its own input
-// and output buffers; the launch reads a device table with one entry per job
-// (the two TMA tensor maps and the job's shape).  Work units are
-// (job, channel, time tile, M tile), M tile fastest, numbered over all jobs;
-// CTA i takes units i, i + G, i + 2G, ... (G = grid size), so the CTAs that
-// run at the same moment work on neighbouring units of the same channel and
-// share its weight and voltage tiles through L2, and every CTA draws a
-// proportional share of every job (load balance without a cost model).
+// and output buffers; the launch reads a table with one entry per job (the
+// two TMA tensor maps and the job's shape), in its parameters or in device
+// memory.  Work units are (job, channel, time tile, M tile), M tile fastest,
+// numbered over all jobs.  Each CTA's producer takes the next unit from a
+// counter in device memory (zeroed before the launch), so the units in
+// flight at any moment are a window of neighbouring units, of one channel
+// of one job most of the time: its weight and voltage tiles are shared
+// through L2, and a CTA that runs slower simply takes fewer units.  (A fixed
+// stride, CTA i taking units i, i + G, ..., let the CTAs drift apart over a
+// long launch: on the 20 sub-array jobs of 128 and 256 antennas of the
+// uneven-batch workload one launch read 135 GB from DRAM against 79 GB for
+// the same jobs launched one at a time.)
 // Every job runs the streamed pipeline (one 128-byte K block of weights and
 // voltages per stage), so any antenna count fits the same kernel; the
-// epilogue and store warp are the single-plan kernel's.  One launch per
-// batch step; it can be captured in a CUDA graph and replayed.
+// epilogue and store warp are the single-plan kernel's.
+//
+// A batch step (bf_batch_execute) sends jobs of fewer than 4 K blocks (the
+// short-K sub-arrays) to their plans' resident-weight kernel instead, on a
+// few forked branches: streaming a 16 KB weight block per stage for a
+// 64-element K block puts three times the single-plan kernel's shared-memory
+// and L2 bytes on every MMA (on the 28 jobs of 16 to 64 antennas of the
+// uneven-batch workload this kernel took 25.8 ms against 20-21 ms for their
+// resident-weight launches).  Of the other jobs, each large one gets a launch
+// of this kernel to itself and the small ones share one launch.  The step
+// can be captured in a CUDA graph and replayed.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -30,6 +44,7 @@ struct BatchArgs {
     int nt, nsplit, wpt, t_int, xst, nacc;
     uint32_t stage_bytes;   // 16384 + nt * 128
     unsigned *err;
+    unsigned long long *next;   // the next unit to take; zero at launch
 };
 
 __device__ __forceinline__ int job_of(const BatchJob *jobs, int n_jobs, long long u)
@@ -43,72 +58,12 @@ __device__ __forceinline__ int job_of(const BatchJob *jobs, int n_jobs, long lon
     return lo;
 }
 
-struct UnitPos {
-    int j, c, tt, m;
-};
-
-// Walks this CTA's units (blockIdx.x, + gridDim.x, ...), decoding positions.
-// Within a job the position advances by the grid size in the mixed radix
-// (M tile, time tile, channel) with additions and carries (the divisions are
-// done once per job).  `fresh` tells the caller that the job changed on the
-// last step, so it reloads its own per-job fields.
-struct UnitWalk {
-    const BatchJob *jobs;
-    long long u, end;
-    int j, mt, t_tiles, m, tt, c, dm, dtt, dc;
-    bool fresh;
-    __device__ void begin(const BatchJob *jobs_)
-    {
-        jobs = jobs_;
-        u = blockIdx.x;
-        j = -1;
-        end = 0;
-        fresh = false;
-    }
-    __device__ bool next(const BatchArgs &a, UnitPos &p)
-    {
-        if (u >= a.total_units) return false;
-        fresh = false;
-        if (j < 0 || u >= end) {
-            j = j < 0 ? job_of(jobs, a.n_jobs, u) : j + 1;
-            while (u >= jobs[j].unit0 + jobs[j].units) ++j;
-            const BatchJob &J = jobs[j];
-            end = J.unit0 + J.units;
-            mt = J.mt;
-            t_tiles = J.t_tiles;
-            const int v = (int)(u - J.unit0);
-            m = v % mt;
-            const int r = v / mt;
-            tt = r % t_tiles;
-            c = r / t_tiles;
-            const int g = (int)gridDim.x;
-            dm = g % mt;
-            dtt = (g / mt) % t_tiles;
-            dc = (g / mt) / t_tiles;
-            fresh = true;
-        }
-        p.j = j;
-        p.m = m;
-        p.tt = tt;
-        p.c = c;
-        u += gridDim.x;
-        // advance to the next unit of this job (garbage past its end: the job
-        // then changes and the position is decoded afresh)
-        m += dm;
-        const int k1 = m >= mt;
-        m -= k1 ? mt : 0;
-        tt += dtt + k1;
-        const int k2 = tt >= t_tiles;
-        tt -= k2 ? t_tiles : 0;
-        c += dc + k2;
-        return true;
-    }
-};
-
-// What the epilogue and the store warp need to know about one tile, written
-// by the producer (which walks the units anyway) into a ring in shared
-// memory, so the 16 epilogue warps carry no walker state (their registers go
-// to the accumulator read-out).
+// What the MMA issuer, the epilogue and the store warp need to know about
+// one tile, written by the producer (which takes the units) into a ring in
+// shared memory, so the 16 epilogue warps carry no unit state (their
+// registers go to the accumulator read-out).  A slot is reused once the
+// consumer of its descriptor (the epilogue group or the store warp) and the
+// MMA issuer have both released it.
 struct __align__(16) TileDesc {
     const float *wscale;   // per-beam power scale rows of the job's first channel, or NULL
     const float *wsig;     // per-beam amplitude scale rows, offset likewise (complex output)
@@ -116,6 +71,8 @@ struct __align__(16) TileDesc {
     const float *acc_in;   // carried-window sums, offset likewise, or NULL
     float *acc_out;
     int b0, n_beams, b_pad, c, tt, T, T_o, c_total, last;   // last != 0: no more tiles
+    int kbn, ks_last;      // the job's K blocks, and MMA k-steps holding antennas in its last block
+    uint32_t idesc;        // the job's MMA instruction descriptor
 };
 constexpr int kDescRing = 16;
 
@@ -145,8 +102,9 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
     const uint32_t b_sempty = b_sfull + 8 * kStageDepth;          // [kStageDepth]
     const uint32_t b_dfull = b_sempty + 8 * kStageDepth;          // [kDescRing]
     const uint32_t b_dempty = b_dfull + 8 * kDescRing;            // [kDescRing]
+    const uint32_t b_mempty = b_dempty + 8 * kDescRing;           // [kDescRing] (the MMA issuer's release)
     uint32_t *tmem_holder =
-        reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth + 2 * kDescRing);
+        reinterpret_cast<uint32_t *>(bars + 2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth + 3 * kDescRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -169,6 +127,7 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
         for (int i = 0; i < kDescRing; ++i) {
             mbar_init(b_dfull + 8 * i, 1);
             mbar_init(b_dempty + 8 * i, DIRECT ? 8 : 1);   // the epilogue group, or the store warp
+            mbar_init(b_mempty + 8 * i, 1);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -184,27 +143,35 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
         if (lane == 0) {
             uint32_t cnt = 0, issued = 0, kt = 0;
             int st = 0;
-            UnitWalk w;
-            w.begin(jobs);
-            UnitPos p;
             bool ok = true;
             const CUtensorMap *xmap = nullptr, *wmap = nullptr;
-            int kbn = 0, ke = 0, t_shift = 0, c_base = 0;
+            int kbn = 0, ke = 0, t_shift = 0, c_base = 0, j = 0, jcur = -1, mt = 1, t_tiles = 1;
+            long long unit0 = 0;
             TileDesc d{};
             const uint32_t bytes = 16384 + a.nt * 128;
-            // publishes one tile descriptor (after the store warp has released the slot)
+            // publishes one tile descriptor (after its last readers have released the slot)
             auto publish = [&](const TileDesc &v) -> bool {
                 const uint32_t slot = kt % kDescRing;
-                if (!mbar_wait(b_dempty + 8 * slot, ((kt / kDescRing) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles))
+                const uint32_t ph = ((kt / kDescRing) & 1u) ^ 1u;
+                if (!mbar_wait(b_dempty + 8 * slot, ph, abort_flag, a.err, kWaitLimitCycles) ||
+                    !mbar_wait(b_mempty + 8 * slot, ph, abort_flag, a.err, kWaitLimitCycles))
                     return false;
                 desc[slot] = v;
                 mbar_arrive(b_dfull + 8 * slot);
                 ++kt;
                 return true;
             };
-            while (ok && w.next(a, p)) {
-                if (w.fresh) {
-                    const BatchJob &J = jobs[p.j];
+            // units from the launch's counter, or (no counter) units blockIdx.x,
+            // + gridDim.x, ...
+            long long u = a.next ? (long long)atomicAdd(a.next, 1ull) : (long long)blockIdx.x;
+            if (u < a.total_units) j = job_of(jobs, a.n_jobs, u);
+            while (ok && u < a.total_units) {
+                // the next unit is taken now; its number is needed after this one's loads
+                const long long u_next = a.next ? (long long)atomicAdd(a.next, 1ull) : u + gridDim.x;
+                while (u >= jobs[j].unit0 + jobs[j].units) ++j;   // units only increase (empty jobs skipped)
+                if (j != jcur) {
+                    jcur = j;
+                    const BatchJob &J = jobs[j];
                     xmap = &J.xmap;
                     wmap = &J.wmap;
                     prefetch_tensormap(xmap);
@@ -213,6 +180,9 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
                     ke = J.ke;
                     t_shift = J.t_shift;
                     c_base = J.c_base;
+                    mt = J.mt;
+                    t_tiles = J.t_tiles;
+                    unit0 = J.unit0;
                     d.wscale = J.wscale ? J.wscale + (size_t)J.c_base * J.b_pad : nullptr;
                     d.wsig = J.wsig + (size_t)J.c_base * J.b_pad;
                     d.out = J.out + (size_t)J.c_base * (CPX ? 2 * (size_t)J.T : (size_t)J.T_o);
@@ -223,10 +193,20 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
                     d.b_pad = J.b_pad;
                     d.T_o = J.T_o;
                     d.c_total = J.c_total;
+                    d.kbn = J.kb;
+                    d.ks_last = J.ks_last;
+                    d.idesc = J.idesc;
                 }
-                d.b0 = p.m * kBeamsPerMTile;
-                d.c = p.c;
-                d.tt = p.tt;
+                // (job, channel, time tile, M tile), M tile fastest (a job has
+                // fewer than 2^31 units: 32-bit divisions)
+                const uint32_t v = (uint32_t)(u - unit0);
+                const int m = (int)(v % (uint32_t)mt);
+                const uint32_t r = v / (uint32_t)mt;
+                const int tt = (int)(r % (uint32_t)t_tiles);
+                const int c = (int)(r / (uint32_t)t_tiles);
+                d.b0 = m * kBeamsPerMTile;
+                d.c = c;
+                d.tt = tt;
                 d.last = 0;
                 if (!publish(d)) break;
                 for (int kb = 0; kb < kbn; ++kb) {
@@ -238,14 +218,16 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
                     issued |= 1u << st;
                     const uint32_t dst = sx + st * a.stage_bytes;
                     mbar_arrive_expect_tx(b_full + 8 * st, bytes);
-                    tma_load_3d(dst, wmap, b_full + 8 * st, kb * ke, p.m * kRowsPerMTile, c_base + p.c);
+                    tma_load_3d(dst, wmap, b_full + 8 * st, kb * ke, m * kRowsPerMTile, c_base + c);
                     // window 0 starts t_shift samples before the chunk: those rows
                     // (negative time coordinates) read as zeros
-                    tma_load_3d(dst + 16384, xmap, b_full + 8 * st, kb * ke, p.tt * a.nt - t_shift, p.c);
+                    tma_load_3d(dst + 16384, xmap, b_full + 8 * st, kb * ke, tt * a.nt - t_shift, c);
                     if (++st == a.xst) st = 0;
                 }
+                u = u_next;
             }
-            // two end markers: one for each epilogue group's next tile
+            // two end markers: one for each epilogue group's next tile (the MMA
+            // issuer stops at the first)
             d.last = 1;
             if (!*abort_flag && publish(d)) publish(d);
             if (*abort_flag)
@@ -255,31 +237,28 @@ __global__ void __maxnreg__(96) k_tc_batch(const BatchArgs a, const __grid_const
         __syncwarp();
     } else if (warp == 1) {
         // ----------------------------------------------------------- MMA issuer
-        // (one issuer: a second one taking alternate units would have to skip
-        // the other's stage fills without waiting, and with units of several
+        // (one issuer: a second one taking alternate tiles would have to skip
+        // the other's stage fills without waiting, and with tiles of several
         // K blocks it can fall two phases behind on a stage, where a parity
         // wait can no longer tell the phases apart)
         if (lane == 0) {
             uint32_t par = 0, tpar = 0;
             int st = 0, acc = 0;
-            UnitWalk w;
-            w.begin(jobs);
-            UnitPos p;
             bool ok = true;
-            int kbn = 0, ks_last = 4;
-            uint32_t idesc = 0;
             // descriptor words of stage 0; a stage's operands are an offset added to the
             // low word (start address in 16-byte units; no carry below 256 KB)
             const uint64_t s_desc0 = sdesc_sw128(sx);
             const uint32_t s_hi = (uint32_t)(s_desc0 >> 32), s_lo0 = (uint32_t)s_desc0;
             const uint32_t stage16 = a.stage_bytes >> 4;
-            while (ok && w.next(a, p)) {
-                if (w.fresh) {
-                    const BatchJob &J = jobs[p.j];
-                    kbn = J.kb;
-                    ks_last = J.ks_last;
-                    idesc = J.idesc;
-                }
+            for (uint32_t kt = 0; ok; ++kt) {
+                // the tile's K extent from its descriptor, then the slot is released
+                const uint32_t slot = kt % kDescRing;
+                if (!mbar_wait(b_dfull + 8 * slot, (kt / kDescRing) & 1u, abort_flag, a.err, kWaitLimitCycles)) break;
+                const TileDesc &D = desc[slot];
+                const int last = D.last, kbn = D.kbn, ks_last = D.ks_last;
+                const uint32_t idesc = D.idesc;
+                mbar_arrive(b_mempty + 8 * slot);
+                if (last) break;
                 if (!mbar_wait(b_tempty + 8 * acc, ((tpar >> acc) & 1u) ^ 1u, abort_flag, a.err, kWaitLimitCycles)) {
                     ok = false;
                     break;
@@ -486,7 +465,7 @@ static int batch_stage_bytes(int nt) { return 16384 + nt * 128; }
 static int batch_layout_end(int xst, int nt)
 {
     return 1024 + xst * batch_stage_bytes(nt) + kStageDepth * kBeamsPerMTile * kMaxWinPerTile * 4 +
-           kDescRing * (int)sizeof(TileDesc) + 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth + 2 * kDescRing) +
+           kDescRing * (int)sizeof(TileDesc) + 8 * (2 * kMaxXStages + 2 * kMaxAcc + 1 + 2 * kStageDepth + 3 * kDescRing) +
            8;
 }
 
@@ -641,6 +620,10 @@ bf_status batch_fill_job(const BatchCore &core, BatchJob *J, const bf_plan *p, c
     J->acc_out = partial ? acc_out : nullptr;
     const bool work = core.cpx ? T > 0 : (T_o + partial) > 0;
     J->units = work ? (long long)c_count * J->t_tiles * J->mt : 0;
+    if (J->units >= (1LL << 31)) {
+        J->units = 0;
+        return set_error(BF_ERR_UNSUPPORTED, "a job of 2^31 or more tiles (split its channels)");
+    }
     if (J->units > 0) {
         if (T == 0) {   // nothing to read: the carried sum passes straight through
             J->units = 0;
@@ -665,9 +648,13 @@ long long batch_index(BatchJob *jobs, int n)
 }
 
 static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, const ParamJobs &pj, int n,
-                               long long total_units, unsigned *d_err, cudaStream_t s)
+                               long long total_units, unsigned *d_err, unsigned long long *d_next, cudaStream_t s)
 {
     if (total_units == 0) return cudaSuccess;
+    if (d_next) {
+        cudaError_t e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s);   // the launch takes units from 0
+        if (e != cudaSuccess) return e;
+    }
     BatchArgs ka;
     ka.jobs = d_jobs;
     ka.n_jobs = n;
@@ -680,42 +667,59 @@ static cudaError_t core_launch(const BatchCore &core, const BatchJob *d_jobs, co
     ka.nacc = core.nacc;
     ka.stage_bytes = (uint32_t)batch_stage_bytes(core.nt);
     ka.err = d_err;
+    ka.next = d_next;
     const int grid = (int)std::min<long long>(core.num_sms, total_units);
     return batch_dispatch(core, BatchLaunch{ka, pj, grid, core.smem, s});
 }
 
 cudaError_t batch_core_launch(const BatchCore &core, const BatchJob *d_jobs, int n, long long total_units,
-                              unsigned *d_err, cudaStream_t s)
+                              unsigned *d_err, unsigned long long *d_next, cudaStream_t s)
 {
     static const ParamJobs unused{};
-    return core_launch(core, d_jobs, unused, n, total_units, d_err, s);
+    return core_launch(core, d_jobs, unused, n, total_units, d_err, d_next, s);
 }
 
 cudaError_t batch_core_launch_params(const BatchCore &core, const BatchJob *jobs, int n, long long total_units,
-                                     unsigned *d_err, cudaStream_t s)
+                                     unsigned *d_err, unsigned long long *d_next, cudaStream_t s)
 {
     if (n < 1 || n > kParamJobs) return cudaErrorInvalidValue;
     ParamJobs pj;
     memcpy((void *)pj.j, (const void *)jobs, sizeof(BatchJob) * n);
-    return core_launch(core, nullptr, pj, n, total_units, d_err, s);
+    return core_launch(core, nullptr, pj, n, total_units, d_err, d_next, s);
 }
 
 cudaError_t batch_core_launch_one(const BatchCore &core, const BatchJob &job, unsigned *d_err, cudaStream_t s)
 {
     BatchJob j = job;
     j.unit0 = 0;
-    return batch_core_launch_params(core, &j, 1, j.units, d_err, s);
+    return batch_core_launch_params(core, &j, 1, j.units, d_err, nullptr, s);
 }
 
 }  // namespace bfi
 
 using namespace bfi;
 
+// Branches of a step for the resident-weight launches: jobs of fewer than 4
+// K blocks run their plan's own kernel (weights resident in shared memory,
+// each voltage tile serving a group of M tiles), several at a time, so the
+// tail of one fills with the CTAs of the next.
+constexpr int kBranches = 4;
+
+// Units per CTA from which a streamed-weight job of a batch step gets a
+// launch of its own (about 100 microseconds of work or more, against a few
+// for a launch in a graph).
+constexpr long long kOwnLaunchRounds = 64;
+
 struct bf_batch {
     std::vector<bf_plan *> plans;
     int n = 0;
     BatchCore core;
-    BatchJob *h_jobs = nullptr;   // pinned, so a captured copy reads it at replay
+    std::vector<char> resident;   // job -> runs the plan's resident-weight kernel, not the persistent launch
+    std::vector<float *> out;
+    cudaStream_t branch[kBranches] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kBranches] = {};
+    BatchJob *h_jobs = nullptr;   // pinned [2n]: the table, then the shared launch's rows (a captured copy reads them at replay)
     std::vector<int> slot;        // job -> its row of the table (rows in order of decreasing K)
     BatchJob *d_jobs = nullptr;
     std::vector<void *> expand_buf;   // per job, FP16 copies of 8/4-bit inputs
@@ -730,6 +734,7 @@ struct bf_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     unsigned *d_err = nullptr;
+    unsigned long long *d_next = nullptr;   // work counter of the persistent launch
 };
 
 static void batch_free(bf_batch *b)
@@ -741,8 +746,14 @@ static void batch_free(bf_batch *b)
     if (b->h_jobs) cudaFreeHost(b->h_jobs);
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_err) cudaFree(b->d_err);
+    if (b->d_next) cudaFree(b->d_next);
     for (void *p : b->expand_buf)
         if (p) cudaFree(p);
+    for (int k = 0; k < kBranches; ++k) {
+        if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     delete b;
 }
 
@@ -786,14 +797,32 @@ bf_status bf_batch_create(bf_batch **out, bf_plan *const *plans, int n_plans, in
     b->slot.assign(n_plans, 0);
     for (int r = 0; r < n_plans; ++r) b->slot[order[r]] = r;
     cudaError_t e;
-    if ((e = cudaHostAlloc((void **)&b->h_jobs, sizeof(BatchJob) * n_plans, cudaHostAllocDefault)) != cudaSuccess ||
+    // pinned table: the rows, then as many staging rows for the shared launch's upload
+    if ((e = cudaHostAlloc((void **)&b->h_jobs, 2 * sizeof(BatchJob) * n_plans, cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_jobs, sizeof(BatchJob) * n_plans)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_err, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_next, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(b->d_err, 0, sizeof(unsigned))) != cudaSuccess) {
         batch_free(b);
         return cuda_error(e, "batch allocation");
     }
-    memset((void *)b->h_jobs, 0, sizeof(BatchJob) * n_plans);
+    b->resident.assign(n_plans, 0);
+    bool any_resident = false;
+    for (int j = 0; j < n_plans; ++j) any_resident |= (b->resident[j] = !plans[j]->tc.stream) != 0;
+    if (any_resident) {
+        if ((e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
+            batch_free(b);
+            return cuda_error(e, "batch event");
+        }
+        for (int k = 0; k < kBranches; ++k)
+            if ((e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming)) != cudaSuccess) {
+                batch_free(b);
+                return cuda_error(e, "batch branch stream");
+            }
+    }
+    b->out.assign(n_plans, nullptr);
+    memset((void *)b->h_jobs, 0, 2 * sizeof(BatchJob) * n_plans);
     b->expand_buf.assign(n_plans, nullptr);
     b->expand_bytes.assign(n_plans, 0);
     b->in.assign(n_plans, nullptr);
@@ -820,7 +849,9 @@ bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
     }
     drop_graph(b);   // a captured step refers to the old inputs
     const void *xin = x;
-    const bool expand = p->dtype == BF_CI8 || p->dtype == BF_CI4;
+    // FP16 widening of 8/4-bit inputs for the persistent launch, and for
+    // resident-weight jobs whose rows TMA cannot read raw
+    const bool expand = (p->dtype == BF_CI8 || p->dtype == BF_CI4) && (!b->resident[job] || p->tc.raw_kb == 0);
     if (expand && T_o > 0) {
         const size_t need = (size_t)p->C * T * p->N * 4;
         if (b->expand_bytes[job] < need) {
@@ -834,10 +865,15 @@ bf_status bf_batch_set(bf_batch *b, int job, const void *x, int T, float *out)
         xin = b->expand_buf[job];
     }
     BatchJob J;
-    bf_status st = batch_fill_job(b->core, &J, p, xin, T, out, 0, nullptr, nullptr);
-    if (st != BF_OK) return st;
+    if (b->resident[job]) {
+        memset((void *)&J, 0, sizeof(J));   // no units in the persistent launch
+    } else {
+        bf_status st = batch_fill_job(b->core, &J, p, xin, T, out, 0, nullptr, nullptr);
+        if (st != BF_OK) return st;
+    }
     b->h_jobs[b->slot[job]] = J;
     b->in[job] = x;
+    b->out[job] = out;
     b->n_samp[job] = T;
     b->set[job] = 1;
     b->total_units = batch_index(b->h_jobs, b->n);
@@ -858,24 +894,99 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
     for (int j = 0; j < b->n; ++j)
         if (!b->set[j]) return set_error(BF_ERR_STATE, "every job needs bf_batch_set before execute");
     cudaStream_t s = (cudaStream_t)stream;
-    if (b->total_units == 0) return BF_OK;
+    // resident-weight jobs with whole windows, most work first
+    std::vector<int> res;
+    for (int j = 0; j < b->n; ++j)
+        if (b->resident[j] && b->n_samp[j] / b->plans[j]->t_int > 0) res.push_back(j);
+    if (b->total_units == 0 && res.empty()) return BF_OK;
+    auto work = [&](int j) { return (double)b->plans[j]->N * b->plans[j]->B * b->plans[j]->C * b->n_samp[j]; };
+    std::stable_sort(res.begin(), res.end(), [&](int x, int y) { return work(x) > work(y); });
     b->last_stream = s;
     b->launched = true;
     cudaError_t e;
-    for (int j = 0; j < b->n; ++j) {
+    auto expand_into = [&](int j, cudaStream_t st) -> cudaError_t {
         const bf_plan *p = b->plans[j];
-        if (b->h_jobs[b->slot[j]].units > 0 && (p->dtype == BF_CI8 || p->dtype == BF_CI4)) {
-            e = launch_expand_to_f16(b->in[j], p->dtype, b->expand_buf[j], (long long)p->C * b->n_samp[j] * p->N,
-                                     p->N, s);
-            if (e != cudaSuccess) return cuda_error(e, "integer expansion");
+        return launch_expand_to_f16(b->in[j], p->dtype, b->expand_buf[j], (long long)p->C * b->n_samp[j] * p->N, p->N,
+                                    st);
+    };
+    auto is_int = [&](int j) { return b->plans[j]->dtype == BF_CI8 || b->plans[j]->dtype == BF_CI4; };
+    if (!res.empty()) {
+        // fork: each job goes to the branch with the least work so far
+        if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return cuda_error(e, "batch fork");
+        double load[kBranches] = {};
+        bool used[kBranches] = {};
+        for (int j : res) {
+            int k = 0;
+            for (int i = 1; i < kBranches; ++i)
+                if (load[i] < load[k]) k = i;
+            load[k] += work(j);
+            cudaStream_t bs = b->branch[k];
+            if (!used[k]) {
+                used[k] = true;
+                if ((e = cudaStreamWaitEvent(bs, b->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "batch fork");
+            }
+            bf_plan *p = b->plans[j];
+            const void *xin = b->in[j];
+            if (is_int(j) && p->tc.raw_kb == 0) {
+                if ((e = expand_into(j, bs)) != cudaSuccess) return cuda_error(e, "integer expansion");
+                xin = b->expand_buf[j];
+            }
+            TcArgs ta;
+            ta.x = xin;
+            ta.c_base = 0;
+            ta.c_launch = p->C;
+            ta.c_total = p->C;
+            ta.T = b->n_samp[j];
+            ta.T_o = b->n_samp[j] / p->t_int;
+            ta.t_int = p->t_int;
+            ta.complex_out = 0;
+            ta.out = b->out[j];
+            ta.err = b->d_err;
+            std::string why;
+            if ((e = launch_tc(p, ta, bs, &why)) != cudaSuccess) {
+                if (!why.empty()) return set_error(BF_ERR_CUDA, "tensor-core kernel (batch job): " + why);
+                return cuda_error(e, "tensor-core kernel (batch job)");
+            }
+        }
+        // join
+        for (int k = 0; k < kBranches; ++k) {
+            if (!used[k]) continue;
+            if ((e = cudaEventRecord(b->ev_join[k], b->branch[k])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, b->ev_join[k], 0)) != cudaSuccess)
+                return cuda_error(e, "batch join");
         }
     }
-    if (b->n <= kParamJobs) {
-        e = batch_core_launch_params(b->core, b->h_jobs, b->n, b->total_units, b->d_err, s);
+    if (b->total_units == 0) return BF_OK;
+    for (int j = 0; j < b->n; ++j)
+        if (!b->resident[j] && b->h_jobs[b->slot[j]].units > 0 && is_int(j))
+            if ((e = expand_into(j, s)) != cudaSuccess) return cuda_error(e, "integer expansion");
+    // Jobs of at least kOwnLaunchRounds units per CTA get a launch of their
+    // own, one after another on the fixed stride: a kernel boundary starts
+    // every CTA on the job together, so the units in flight stay within a
+    // channel or two.  The rest share one launch on the work counter.
+    std::vector<BatchJob> rows;
+    long long shared_units = 0;
+    for (int r = 0; r < b->n; ++r) {
+        BatchJob J = b->h_jobs[r];
+        if (J.units == 0) continue;
+        if (J.units >= kOwnLaunchRounds * (long long)b->core.num_sms) {
+            if ((e = batch_core_launch_one(b->core, J, b->d_err, s)) != cudaSuccess)
+                return cuda_error(e, "batched tensor-core kernel");
+            continue;
+        }
+        J.unit0 = shared_units;
+        shared_units += J.units;
+        rows.push_back(J);
+    }
+    if (rows.empty()) return BF_OK;
+    if ((int)rows.size() <= kParamJobs) {
+        e = batch_core_launch_params(b->core, rows.data(), (int)rows.size(), shared_units, b->d_err, b->d_next, s);
     } else {
-        e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * b->n, cudaMemcpyHostToDevice, s);
+        BatchJob *dst = b->h_jobs + b->n;   // the staging rows behind the table
+        std::copy(rows.begin(), rows.end(), dst);
+        e = cudaMemcpyAsync(b->d_jobs, dst, sizeof(BatchJob) * rows.size(), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_error(e, "batch table upload");
-        e = batch_core_launch(b->core, b->d_jobs, b->n, b->total_units, b->d_err, s);
+        e = batch_core_launch(b->core, b->d_jobs, (int)rows.size(), shared_units, b->d_err, b->d_next, s);
     }
     if (e != cudaSuccess) return cuda_error(e, "batched tensor-core kernel");
     return BF_OK;

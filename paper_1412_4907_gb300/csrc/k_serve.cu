@@ -114,6 +114,7 @@ struct Stream {   // one configuration: its plan and its open window
 struct Slot {
     BatchJob *h_jobs = nullptr;   // the step's job table (passed in the launch parameters)
     unsigned *d_err = nullptr;
+    unsigned long long *d_next = nullptr;   // the step launch's work counter
     unsigned *h_err = nullptr;    // pinned
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
     std::vector<Request *> reqs;
@@ -300,7 +301,7 @@ static std::string launch_step(bf_server *s, Slot &sl)
     // sit in the host-to-device queue behind the chunks admitted for later
     // steps and hold this launch back
     if ((e = cudaEventRecord(sl.ev_k0, s->s_k)) != cudaSuccess ||
-        (e = n <= kParamJobs ? batch_core_launch_params(s->core, sl.h_jobs, n, units, sl.d_err, s->s_k)
+        (e = n <= kParamJobs ? batch_core_launch_params(s->core, sl.h_jobs, n, units, sl.d_err, sl.d_next, s->s_k)
                              : cudaErrorInvalidValue) != cudaSuccess ||
         (e = cudaEventRecord(sl.ev_k1, s->s_k)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s->s_out, sl.ev_k1, 0)) != cudaSuccess)
@@ -485,6 +486,7 @@ static void server_free(bf_server *s)
     for (Slot &sl : s->slots) {
         if (sl.h_jobs) cudaFreeHost(sl.h_jobs);
         if (sl.d_err) cudaFree(sl.d_err);
+        if (sl.d_next) cudaFree(sl.d_next);
         if (sl.h_err) cudaFreeHost(sl.h_err);
         if (sl.ev_k0) cudaEventDestroy(sl.ev_k0);
         if (sl.ev_k1) cudaEventDestroy(sl.ev_k1);
@@ -557,6 +559,7 @@ bf_status bf_server_create(bf_server **out, bf_plan *const *plans, int n_configs
         if ((e = cudaHostAlloc((void **)&sl.h_jobs, sizeof(BatchJob) * n_configs, cudaHostAllocDefault)) ==
                 cudaSuccess &&
             (e = cudaMalloc((void **)&sl.d_err, sizeof(unsigned))) == cudaSuccess &&
+            (e = cudaMalloc((void **)&sl.d_next, sizeof(unsigned long long))) == cudaSuccess &&
             (e = cudaHostAlloc((void **)&sl.h_err, sizeof(unsigned), cudaHostAllocDefault)) == cudaSuccess &&
             (e = cudaEventCreate(&sl.ev_k0)) == cudaSuccess)
             e = cudaEventCreate(&sl.ev_k1);

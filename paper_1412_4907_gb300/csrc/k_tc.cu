@@ -189,7 +189,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     ka.wscale = f.qmax > 0.f ? p->d_wscale : nullptr;   // unscaled formats multiply by 1
     ka.wsig = p->d_wsig;
     ka.out = ta.out;
-    ka.err = p->d_err;
+    ka.err = ta.err ? ta.err : p->d_err;
     ka.raw_kb = cfg.raw_kb;
     ka.raw_stage_bytes = (uint32_t)(f.kb * cfg.nt * cfg.raw_kb);
     if (ka.ct_total == 0) return cudaSuccess;
@@ -203,7 +203,7 @@ cudaError_t launch_tc(bf_plan *p, const TcArgs &ta, cudaStream_t s, std::string 
     const int grid = (int)(n_sets * ka.gq);
     const bool f8 = f.op == kOpE4M3;
     const int win = (ta.t_int == 64 || ta.t_int == 32 || ta.t_int == 16) ? ta.t_int : (ta.t_int % 16 == 0 ? 0 : -1);
-const bool cpx = ta.complex_out != 0;
+    const bool cpx = ta.complex_out != 0;
     if (f8) return launch_tc_family<true, 0>(xm, wm, ka, win, cpx, grid, cfg.smem, s);
     switch (widen ? p->dtype : 0) {
     case BF_CI8: return launch_tc_family<false, BF_CI8>(xm, wm, ka, win, cpx, grid, cfg.smem, s);

@@ -1,5 +1,7 @@
-"""GPU parity of the batched persistent launch (``bf_batch_*``).
+"""GPU parity of batched execution (``bf_batch_*``).
 
+A batch step runs the jobs of 4 or more K blocks in one persistent launch and
+the others through their plans' resident-weight kernel on forked streams.
 Each job of a batch is checked against the FP64 oracle for its own plan (the
 tolerances of the single-plan parity tests) and against the same plan run
 alone through ``bf_execute``: batching changes where a tile is computed, not
@@ -83,19 +85,33 @@ def run_batch(bf, jobs, tile_t=0):
     return batch, [o.cpu().numpy() for o in outs]
 
 
+def streamed(bf, plan):
+    """The plan's weights are streamed (4 or more K blocks): its batch jobs
+    run in the persistent launch."""
+    return bf.bf_plan_query_tiles(plan.handle)["x_stages"] == 0
+
+
 def test_batch_mixed_fp16_family(bf):
     """FP16, int8 and int4 plans of different antenna counts (1 to 8 K
     blocks), beam counts (partial M tiles), channel counts and sample counts
-    (ragged time tiles, a job shorter than one window, an empty job)."""
+    (ragged time tiles, a job shorter than one window, an empty job).  The
+    int8 job of 36 antennas and the int4 job of 24 have rows TMA cannot read
+    raw (72 and 24 bytes): they are widened to FP16 before their
+    resident-weight launch; the other 8/4-bit resident jobs are widened in
+    the kernel."""
     specs = [(synth.C16F, 64, 100, 3, 640), (synth.C16F, 256, 70, 2, 300), (synth.CI8, 40, 130, 2, 512),
              (synth.CI4, 32, 64, 2, 200), (synth.C16F, 8, 1, 1, 64), (synth.C16F, 16, 20, 1, 30),
-             (synth.CI8, 128, 65, 1, 0)]
+             (synth.CI8, 128, 65, 1, 0), (synth.CI8, 36, 30, 1, 256), (synth.CI4, 24, 20, 2, 128),
+             (synth.CI8, 160, 40, 2, 384)]
     jobs = [Job(bf, m, n, b, c, t, 64, seed=20 + i) for i, (m, n, b, c, t) in enumerate(specs)]
     batch, outs = run_batch(bf, jobs)
     q = batch.query()
     assert q["tile_t"] == 256
-    # time tiles cover whole windows only: the tail beyond the last window is never read
-    exp_units = sum(j.scene.freqs.size * -(-(j.T // 64 * 64) // 256) * -(-j.dirs.shape[0] // 64) for j in jobs)
+    assert [streamed(bf, j.plan) for j in jobs] == [False, True, False, False, False, False, True, False, False, True]
+    # units of the persistent launch; time tiles cover whole windows only (the
+    # tail beyond the last window is never read)
+    exp_units = sum(j.scene.freqs.size * -(-(j.T // 64 * 64) // 256) * -(-j.dirs.shape[0] // 64)
+                    for j in jobs if streamed(bf, j.plan))
     assert q["units"] == exp_units
     for i, (j, P) in enumerate(zip(jobs, outs)):
         check_job(f"job{i}", P, j)
@@ -133,17 +149,22 @@ def test_batch_windows_and_tiles(bf, t_int, tile_t):
 
 
 def test_batch_many_small_jobs(bf):
-    """More jobs than SMs, so CTAs straddle job boundaries and the cost split
-    lands inside and between jobs; includes empty jobs."""
+    """More persistent-launch jobs than SMs (and than fit in the launch
+    parameters), so CTAs straddle job boundaries and the cost split lands
+    inside and between jobs, beside dozens of resident-weight jobs on the
+    forked streams; includes empty jobs."""
     rng = np.random.default_rng(5)
     jobs = []
     for i in range(180):
-        n = int(rng.choice([4, 8, 12, 32, 68]))
+        n = int(rng.choice([4, 8, 12, 32, 68, 100, 132, 200], p=[.05, .05, .05, .05, .1, .3, .2, .2]))
         b = int(rng.integers(1, 90))
         c = int(rng.integers(1, 3))
         t = int(rng.choice([0, 64, 100, 256, 300]))
         jobs.append(Job(bf, synth.C16F, n, b, c, t, 64, seed=100 + i))
+    n_streamed = sum(streamed(bf, j.plan) and j.T >= 64 for j in jobs)
+    assert n_streamed > 152 // 2 and n_streamed > 64 and len(jobs) - n_streamed > 20
     batch, outs = run_batch(bf, jobs)
+    assert batch.query()["units"] > 152
     for i, (j, P) in enumerate(zip(jobs, outs)):
         check_job(f"small{i}", P, j)
     batch.close()
@@ -154,7 +175,7 @@ def test_batch_graph_replay_and_weights(bf):
     up weights regenerated by bf_weights on a member plan; re-binding a job
     drops the graph."""
     stream = torch.cuda.Stream()
-    specs = [(synth.C16F, 64, 64, 2, 512), (synth.CI8, 32, 100, 1, 256)]
+    specs = [(synth.C16F, 64, 64, 2, 512), (synth.CI8, 32, 100, 1, 256), (synth.C16F, 160, 40, 1, 320)]
     jobs = [Job(bf, m, n, b, c, t, 64, seed=80 + i) for i, (m, n, b, c, t) in enumerate(specs)]
     with torch.cuda.stream(stream):
         batch = bf.Batch([j.plan for j in jobs], stream=stream)
@@ -179,6 +200,7 @@ def test_batch_graph_replay_and_weights(bf):
         batch.sync()
         check_job("replay_new0", outs[0].cpu().numpy(), jobs[0], jobs[0].oracle(new_dirs))
         check_job("replay_new1", outs[1].cpu().numpy(), jobs[1])
+        check_job("replay_new2", outs[2].cpu().numpy(), jobs[2])
         batch.set(1, jobs[1].x, out=outs[1], n_samp=jobs[1].T)
         with pytest.raises(bf.BFError) as ei:
             batch.replay()
