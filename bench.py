@@ -629,26 +629,34 @@ def batched_measure(args, emit=True):
         d.update(extra)
         print(json.dumps(d), flush=True)
 
-    # fixed tiles
-    batch = bf.Batch(plans, tile_t=128, stream=stream)
-    for j, (x, o, T) in enumerate(zip(xs, outs, n_samps)):
-        batch.set(j, x, o, n_samp=T)
-    batch.capture()
-    ms_fixed = timed(batch.replay)
-    batch.sync()
-    line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": step_launches}, "fixed_128")
-    batch.close()
-    # autotuned
-    tuned = tune.tune_batch(plans, xs, outs, n_samps, stream=stream, reps=3, cache=None)
+    if args.batched_tile:
+        # one given tile width only: no fixed-width variant, no tuning (the
+        # first launches of the run are then the measured steps: for profiling)
+        ms_fixed = None
+        tuned = {"tile_t": args.batched_tile, "table": []}
+    else:
+        # fixed tiles
+        batch = bf.Batch(plans, tile_t=128, stream=stream)
+        for j, (x, o, T) in enumerate(zip(xs, outs, n_samps)):
+            batch.set(j, x, o, n_samp=T)
+        batch.capture()
+        ms_fixed = timed(batch.replay)
+        batch.sync()
+        line("batched, fixed 128-sample tiles", ms_fixed, {"tile_t": 128, "gpu_launches_per_step": step_launches},
+             "fixed_128")
+        batch.close()
+        # autotuned
+        tuned = tune.tune_batch(plans, xs, outs, n_samps, stream=stream, reps=3, cache=None)
     batch = bf.Batch(plans, tile_t=tuned["tile_t"], stream=stream)
     for j, (x, o, T) in enumerate(zip(xs, outs, n_samps)):
         batch.set(j, x, o, n_samp=T)
     batch.capture()
     ms_tuned = timed(batch.replay)
     batch.sync()
-    line("batched, autotuned tile", ms_tuned, {"tile_t": tuned["tile_t"], "tuning_table": tuned["table"],
-                                                "speedup_vs_fixed": ms_fixed / ms_tuned,
-                                                "gpu_launches_per_step": step_launches},
+    line("batched, autotuned tile" if not args.batched_tile else f"batched, {args.batched_tile}-sample tiles",
+         ms_tuned, {"tile_t": tuned["tile_t"], "tuning_table": tuned["table"],
+                    "speedup_vs_fixed": ms_fixed / ms_tuned if ms_fixed else None,
+                    "gpu_launches_per_step": step_launches},
          "autotuned")
     # one plan at a time
     def per_plan():
@@ -1037,6 +1045,8 @@ def main():
                     help="weak: every rank beamforms its own chunk; strong: the chunk's channels are split over ranks")
     ap.add_argument("--batched-ant", default="",
                     help="batched: only the jobs with these antenna counts (comma list; diagnostics)")
+    ap.add_argument("--batched-tile", type=int, default=0,
+                    help="batched: this tile width only, no fixed-width variant or tuning (profiling)")
     ap.add_argument("--batched-chan-div", type=int, default=1,
                     help="divide every job's channel count (smaller case of the same jobs, for profiling)")
     ap.add_argument("--peaks", action="store_true",
