@@ -6,15 +6,16 @@
 // and output buffers; the launch reads a table with one entry per job (the
 // two TMA tensor maps and the job's shape), in its parameters or in device
 // memory.  Work units are (job, channel, time tile, M tile), M tile fastest,
-// numbered over all jobs.  Each CTA's producer takes the next unit from a
-// counter in device memory (zeroed before the launch), so the units in
-// flight at any moment are a window of neighbouring units, of one channel
-// of one job most of the time: its weight and voltage tiles are shared
-// through L2, and a CTA that runs slower simply takes fewer units.  (A fixed
-// stride, CTA i taking units i, i + G, ..., let the CTAs drift apart over a
-// long launch: on the 20 sub-array jobs of 128 and 256 antennas of the
-// uneven-batch workload one launch read 135 GB from DRAM against 79 GB for
-// the same jobs launched one at a time.)
+// numbered over all jobs.  In a launch over several jobs each CTA's producer
+// takes the next unit from a counter in device memory (zeroed before the
+// launch), so the units in flight at any moment are a window of neighbouring
+// units, of one channel of one job most of the time: its weight and voltage
+// tiles are shared through L2, and a CTA that runs slower simply takes fewer
+// units.  (A fixed stride, CTA i taking units i, i + G, ..., let the CTAs
+// drift apart over a long launch: on the 20 sub-array jobs of 128 and 256
+// antennas of the uneven-batch workload one launch read 135 GB from DRAM
+// against 79 GB for the same jobs launched one at a time.)  A launch over
+// one job keeps the fixed stride, which measured faster there.
 // Every job runs the streamed pipeline (one 128-byte K block of weights and
 // voltages per stage), so any antenna count fits the same kernel; the
 // epilogue and store warp are the single-plan kernel's.
@@ -915,6 +916,7 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
         if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return cuda_error(e, "batch fork");
         double load[kBranches] = {};
         bool used[kBranches] = {};
+        bf_status st = BF_OK;
         for (int j : res) {
             int k = 0;
             for (int i = 1; i < kBranches; ++i)
@@ -922,13 +924,19 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
             load[k] += work(j);
             cudaStream_t bs = b->branch[k];
             if (!used[k]) {
+                if ((e = cudaStreamWaitEvent(bs, b->ev_fork, 0)) != cudaSuccess) {
+                    st = cuda_error(e, "batch fork");
+                    break;
+                }
                 used[k] = true;
-                if ((e = cudaStreamWaitEvent(bs, b->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "batch fork");
             }
             bf_plan *p = b->plans[j];
             const void *xin = b->in[j];
             if (is_int(j) && p->tc.raw_kb == 0) {
-                if ((e = expand_into(j, bs)) != cudaSuccess) return cuda_error(e, "integer expansion");
+                if ((e = expand_into(j, bs)) != cudaSuccess) {
+                    st = cuda_error(e, "integer expansion");
+                    break;
+                }
                 xin = b->expand_buf[j];
             }
             TcArgs ta;
@@ -944,17 +952,20 @@ bf_status bf_batch_execute(bf_batch *b, void *stream)
             ta.err = b->d_err;
             std::string why;
             if ((e = launch_tc(p, ta, bs, &why)) != cudaSuccess) {
-                if (!why.empty()) return set_error(BF_ERR_CUDA, "tensor-core kernel (batch job): " + why);
-                return cuda_error(e, "tensor-core kernel (batch job)");
+                st = why.empty() ? cuda_error(e, "tensor-core kernel (batch job)")
+                                 : set_error(BF_ERR_CUDA, "tensor-core kernel (batch job): " + why);
+                break;
             }
         }
-        // join
+        // join (also after a failure, so `stream` still covers what was enqueued)
         for (int k = 0; k < kBranches; ++k) {
             if (!used[k]) continue;
             if ((e = cudaEventRecord(b->ev_join[k], b->branch[k])) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(s, b->ev_join[k], 0)) != cudaSuccess)
-                return cuda_error(e, "batch join");
+                (e = cudaStreamWaitEvent(s, b->ev_join[k], 0)) != cudaSuccess) {
+                if (st == BF_OK) st = cuda_error(e, "batch join");
+            }
         }
+        if (st != BF_OK) return st;
     }
     if (b->total_units == 0) return BF_OK;
     for (int j = 0; j < b->n; ++j)

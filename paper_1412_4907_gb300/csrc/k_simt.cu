@@ -10,6 +10,8 @@
 // for any other T_int, in which antennas are staged through shared memory 16
 // at a time and a block owns whole integration windows, summing |B|^2 of
 // each window in ascending sample order (deterministic).
+#include <type_traits>
+
 #include "bf_internal.h"
 
 namespace bfi {
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(256) k_simt(const float2 *__restrict__ X, cons
 // each thread squares its 4 samples of 4 beams and the window sums are
 // reduced across the WIN / 4 lanes that hold the window, in a fixed order.
 constexpr int kKA = 32;   // antennas per pipeline step
-constexpr int kRun = 16;  // sub-tiles (1024 samples) per block
+constexpr int kRun = 16;  // sub-tiles (1024 samples) per block; twice that with resident weights
 constexpr int kPB = 128;  // beams per block of the pipelined form
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
@@ -161,34 +163,41 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool val
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <bool NCT, bool COMPLEX, int WIN>
+// RES (N <= kKA: the weights are loaded once and stay): four voltage stages,
+// one barrier per step and runs of 32 sub-tiles per block; otherwise two
+// stages of voltages and of weights, a second barrier that frees a stage
+// for the step after next, and runs of 16 sub-tiles.
+template <bool NCT, bool COMPLEX, int WIN, bool RES>
 __global__ void __launch_bounds__(256, 2)
     k_simt_pipe(const float2 *__restrict__ X, const float2 *__restrict__ W, float *__restrict__ out, int N,
                 int c_base, int c_in_stride, int c_total, int B, int b_pad, int T, int T_o, int t_end)
 {
-    // dynamic shared memory (100 KB): two stages of voltages and of weights
+    // dynamic shared memory (100 KB either way): voltage stages, then weight stages
+    constexpr int XS = RES ? 4 : 2;
     extern __shared__ __align__(16) float2 pipe_smem[];
     auto sX = reinterpret_cast<float2(*)[kKA][kST + kPad]>(pipe_smem);
-    auto sW = reinterpret_cast<float2(*)[kKA][kPB + kPad]>(pipe_smem + 2 * kKA * (kST + kPad));
+    auto sW = reinterpret_cast<float2(*)[kKA][kPB + kPad]>(pipe_smem + XS * kKA * (kST + kPad));
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int c = blockIdx.z;
     const int cg = c_base + c;
     const int b0 = blockIdx.y * kPB;
-    const int sub0 = blockIdx.x * kRun;
-    const int n_sub = min(kRun, (t_end - sub0 * kST + kST - 1) / kST);
-    const int n_chunk = (N + kKA - 1) / kKA;
+    constexpr int RUN = RES ? 2 * kRun : kRun;
+    const int sub0 = blockIdx.x * RUN;
+    const int n_sub = min(RUN, (t_end - sub0 * kST + kST - 1) / kST);
+    const int n_chunk = RES ? 1 : (N + kKA - 1) / kKA;
     const bool w_resident = n_chunk == 1;
     const int n_step = n_sub * n_chunk;
     const float2 *Wc = W + ((size_t)cg * b_pad + b0) * N;
 
-    // issue the copies of step q (sub-tile q / n_chunk, antenna chunk q % n_chunk) into stage q & 1
+    // issue the copies of step q (sub-tile q / n_chunk, antenna chunk q % n_chunk) into stage q % XS
     auto load = [&](int q) {
-        const int st = q & 1;
+        const int st = q % XS;
         const int sub = sub0 + q / n_chunk, a0 = (q % n_chunk) * kKA;
         const int t0 = sub * kST;
         for (int i = tid; i < kKA * kST; i += 256) {
@@ -210,31 +219,38 @@ __global__ void __launch_bounds__(256, 2)
             for (int i = tid; i < kKA * kPB; i += 256) {
                 const int bl = i / kKA, a = i % kKA;
                 const bool ok = a0 + a < N && b0 + bl < b_pad;   // rows past the padded beams read zero
-                cp_async8(&sW[st][a][bl], Wc + (ok ? (size_t)bl * N + a0 + a : 0), ok);
+                cp_async8(&sW[RES ? 0 : st][a][bl], Wc + (ok ? (size_t)bl * N + a0 + a : 0), ok);
             }
         cp_async_commit();
     };
 
     float2 acc[8][4];
     load(0);
+    if (RES && n_step > 1) load(1);
+    if (RES && n_step > 2) load(2);
     for (int q = 0; q < n_step; ++q) {
-        if (q + 1 < n_step) {
-            load(q + 1);
-            cp_async_wait1();
+        if (RES) {
+            // steps q and q + 1 are in flight; the barrier also tells that every
+            // thread has finished step q - 1, whose stage load(q + 2) refills
+            if (q + 2 < n_step) cp_async_wait2();
+            else if (q + 1 < n_step) cp_async_wait1();
+            else cp_async_wait0();
+            __syncthreads();
+            if (q + 3 < n_step) load(q + 3);
         } else {
-            cp_async_wait0();
+            if (q + 1 < n_step) {
+                load(q + 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int st = q & 1, k = q % n_chunk;
+        const int st = q % XS, k = q % n_chunk;
         const int ws = w_resident ? 0 : st;
-        if (k == 0) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-        }
-#pragma unroll 1
-        for (int a = 0; a < kKA; ++a) {
+        // one antenna: 8 beams x 4 samples of complex multiply-adds; the first
+        // antenna of a sub-tile starts the sums with products (no zeroing)
+        auto mac = [&](int a, auto first) {
             float2 w[8];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -250,12 +266,24 @@ __global__ void __launch_bounds__(256, 2)
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    acc[i][j].x = fmaf(w[i].x, x[j].x, acc[i][j].x);
+                    if constexpr (decltype(first)::value) {
+                        acc[i][j].x = __fmul_rn(w[i].x, x[j].x);
+                        acc[i][j].y = __fmul_rn(w[i].x, x[j].y);
+                    } else {
+                        acc[i][j].x = fmaf(w[i].x, x[j].x, acc[i][j].x);
+                        acc[i][j].y = fmaf(w[i].x, x[j].y, acc[i][j].y);
+                    }
                     acc[i][j].x = fmaf(-w[i].y, x[j].y, acc[i][j].x);
-                    acc[i][j].y = fmaf(w[i].x, x[j].y, acc[i][j].y);
                     acc[i][j].y = fmaf(w[i].y, x[j].x, acc[i][j].y);
                 }
+        };
+        int a_first = 0;
+        if (k == 0) {
+            mac(0, std::true_type{});
+            a_first = 1;
         }
+#pragma unroll 1
+        for (int a = a_first; a < kKA; ++a) mac(a, std::false_type{});
         if (k == n_chunk - 1) {
             const int t_sub = (sub0 + q / n_chunk) * kST;
             if (COMPLEX) {
@@ -283,7 +311,7 @@ __global__ void __launch_bounds__(256, 2)
                 }
             }
         }
-        __syncthreads();   // the stage is free for step q + 2
+        if (!RES) __syncthreads();   // the stage is free for step q + 2
     }
 }
 
@@ -298,18 +326,22 @@ cudaError_t launch_simt_range(bf_plan *p, const void *x, int c_base, int c_launc
         const int t_end = complex_out ? T : T_o * t_int;
         const int n_sub = (t_end + kST - 1) / kST;
         if (n_sub == 0 || c_launch == 0) return cudaSuccess;
-        dim3 grid((n_sub + kRun - 1) / kRun, (p->wf.b_pad + kPB - 1) / kPB, c_launch);
+        const int run = p->N <= kKA ? 2 * kRun : kRun;   // sub-tiles per block (the kernel's RUN)
+        dim3 grid((n_sub + run - 1) / run, (p->wf.b_pad + kPB - 1) / kPB, c_launch);
         const float2 *X = reinterpret_cast<const float2 *>(x);
         const float2 *W = reinterpret_cast<const float2 *>(p->d_w);
         const int c_in_stride = nct ? p->C : c_launch;
-        const int pipe_smem = (int)(sizeof(float2) * 2 * kKA * ((kST + kPad) + (kPB + kPad)));
-#define BF_SIMT_PIPE(NCTV, CPX, WV)                                                                            \
-    do {                                                                                                       \
-        cudaError_t e_ = cudaFuncSetAttribute(k_simt_pipe<NCTV, CPX, WV>,                                      \
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, pipe_smem);         \
-        if (e_ != cudaSuccess) return e_;                                                                      \
-        k_simt_pipe<NCTV, CPX, WV><<<grid, 256, pipe_smem, s>>>(X, W, out, p->N, c_base, c_in_stride, p->C, p->B, \
-                                                            p->wf.b_pad, T, T_o, t_end);                       \
+        // up to kKA antennas the weights stay resident: three voltage stages, one weight stage
+        const bool res = p->N <= kKA;
+        const int pipe_smem = res ? (int)(sizeof(float2) * kKA * (4 * (kST + kPad) + (kPB + kPad)))
+                                  : (int)(sizeof(float2) * 2 * kKA * ((kST + kPad) + (kPB + kPad)));
+#define BF_SIMT_PIPE(NCTV, CPX, WV)                                                                             \
+    do {                                                                                                        \
+        auto k_ = res ? k_simt_pipe<NCTV, CPX, WV, true> : k_simt_pipe<NCTV, CPX, WV, false>;                   \
+        cudaError_t e_ = cudaFuncSetAttribute(k_, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe_smem);      \
+        if (e_ != cudaSuccess) return e_;                                                                       \
+        k_<<<grid, 256, pipe_smem, s>>>(X, W, out, p->N, c_base, c_in_stride, p->C, p->B, p->wf.b_pad, T, T_o,  \
+                                        t_end);                                                                 \
     } while (0)
 #define BF_SIMT_PIPE_W(NCTV)                          \
     do {                                              \
