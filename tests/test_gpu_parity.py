@@ -178,6 +178,33 @@ def test_fp32_complex_and_nct(bf):
     check("fp32_nct", Pn, oracle.power(W, X64, 8), synth.C32)
 
 
+@pytest.mark.parametrize("n_ant,t_int,n_samp", [
+    (32, 64, 2577),   # weights resident: 40 sub-tiles, so a block of 32 and a ragged one of 8 per beam block
+    (33, 16, 700),    # two 32-antenna chunks, the second holding one antenna
+    (80, 32, 530),    # three chunks, the last half full
+])
+def test_fp32_pipeline_chunks_and_runs(bf, n_ant, t_int, n_samp):
+    """The pipelined FP32 form outside the real-time shape: the resident-weight
+    schedule over more than one block of sub-tiles, and the streamed-weight
+    schedule over several antenna chunks (partial last chunk), with 150 beams
+    (two 128-beam blocks, the second partial), powers and complex beams."""
+    scene = small_scene(n_ant=n_ant, n_chan=2, n_samp=n_samp, grid=False)
+    dirs = synth.beam_grid(15, 10)
+    x, X64 = stored_voltages(scene, synth.C32)
+    P, q = run_power(bf, scene, dirs, t_int, synth.C32, x)
+    assert q["kernel"] == bf.BF_KERNEL_SIMT
+    W = oracle.weights(scene.pos, scene.freqs, dirs)
+    check(f"fp32_pipe_n{n_ant}", P, oracle.power(W, X64, t_int), synth.C32)
+    plan = bf.Plan(scene.pos, scene.freqs, dirs, bf.BF_C32, t_int)
+    Bg = plan.execute_complex(dev(x)).cpu().numpy()
+    plan.close()
+    Bg = Bg[..., 0] + 1j * Bg[..., 1]
+    Bref = oracle.beams(W, X64)
+    err = np.max(np.abs(Bg - Bref)) / np.max(np.abs(Bref))
+    record("fp32_pipe_complex", float(err), 0.0, mode="c32")
+    assert err < 2e-6
+
+
 # ---------------------------------------------------------- tensor-core path
 @pytest.mark.parametrize("mode", MODES_TC)
 def test_tc_modes_ragged(bf, mode):
