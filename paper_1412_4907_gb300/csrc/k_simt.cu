@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(256, 2)
     if (RES && n_step > 2) load(2);
     for (int q = 0; q < n_step; ++q) {
         if (RES) {
-            // steps q and q + 1 are in flight; the barrier also tells that every
-            // thread has finished step q - 1, whose stage load(q + 2) refills
+            // steps q .. q + 2 are in flight; the barrier also tells that every
+            // thread has finished step q - 1, whose stage load(q + 3) refills
             if (q + 2 < n_step) cp_async_wait2();
             else if (q + 1 < n_step) cp_async_wait1();
             else cp_async_wait0();
